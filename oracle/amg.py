@@ -1,0 +1,224 @@
+"""Smoothed-aggregation AMG, plain FP64 (oracle; test infrastructure only).
+
+The paper approximates each diagonal-block subsolve (M + h A~_jj F) w_j = v_j
+by one AMG V-cycle (Section 4.2) using smoothed aggregation from IFISS
+(Section 5).  The paper gives no further parameters; this module follows the
+reading fixed in the design notes, step by step:
+
+  strength   i ~ j strong iff  (|a_ij| + |a_ji|)/2 >= theta sqrt(|a_ii a_jj|)
+             (symmetrised so that nonsymmetric blocks give an undirected
+             graph; theta = 0.08 by default).
+  roots      a maximal distance-2 independent set of the strength graph,
+             chosen greedily in decreasing priority; priority of node i on
+             level l is the 64-bit key (fmix32(i ^ (0x9E3779B9*(l+1))) << 32) | i
+             where fmix32 is the MurmurHash3 32-bit finaliser.
+  aggregates each root and its strong neighbours form an aggregate (phase 1);
+             every other node joins the aggregate of its phase-1 strong
+             neighbour of largest priority (phase 2).  Aggregates are
+             numbered by increasing root index.
+  P          tentative piecewise constant P_t (entries 1), smoothed once:
+             P = (I - omega D^{-1} A) P_t, omega = 4 / (3 rho),
+             rho = max_i sum_j |a_ij| / |a_ii|.
+  coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max; the
+             coarsest level is solved directly (dense LU).
+  smoother   l1-Jacobi x <- x + D_l1^{-1} (b - A x), D_l1 = diag(sum_j |a_ij|),
+             or Chebyshev of degree k on the l1-scaled operator D_l1^{-1} A,
+             whose spectrum lies in (0, 1] for symmetric A (D_l1 - A is
+             diagonally dominant); the interval [lo, 1] (lo = 0.1) is fixed, so
+             no eigenvalue estimate is needed.  The Chebyshev recurrence is
+             the classical three-term one (Saad, Iterative Methods, Alg. 12.1):
+               theta = (1+lo)/2, delta = (1-lo)/2, sigma = theta/delta,
+               rho_0 = 1/sigma, d_0 = D^{-1}(b - A x_0)/theta, x_1 = x_0 + d_0,
+               rho_k = 1/(2 sigma - rho_{k-1}),
+               d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k/delta) D^{-1}(b - A x_k),
+               x_{k+1} = x_k + d_k.
+             V(nu1, nu2) cycle from a zero initial guess (each sweep is one
+             l1-Jacobi step or one Chebyshev polynomial of degree k).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+M32 = 0xFFFFFFFF
+
+
+def fmix32(x: int) -> int:
+    """MurmurHash3 32-bit finaliser (Appleby), on a Python int."""
+    x &= M32
+    x ^= x >> 16
+    x = (x * 0x85EBCA6B) & M32
+    x ^= x >> 13
+    x = (x * 0xC2B2AE35) & M32
+    x ^= x >> 16
+    return x
+
+
+def priority_keys(n: int, level: int) -> np.ndarray:
+    """64-bit priority keys of nodes 0..n-1 on ``level`` (unique)."""
+    salt = (0x9E3779B9 * (level + 1)) & M32
+    x = (np.arange(n, dtype=np.uint64) ^ np.uint64(salt)) & np.uint64(M32)
+    x ^= x >> np.uint64(16)
+    x = (x * np.uint64(0x85EBCA6B)) & np.uint64(M32)
+    x ^= x >> np.uint64(13)
+    x = (x * np.uint64(0xC2B2AE35)) & np.uint64(M32)
+    x ^= x >> np.uint64(16)
+    return (x << np.uint64(32)) | np.arange(n, dtype=np.uint64)
+
+
+def strength_graph(A: sp.csr_matrix, theta: float) -> sp.csr_matrix:
+    """Boolean symmetric strength graph (no diagonal) as CSR with sorted
+    indices."""
+    A = A.tocsr()
+    A.sort_indices()
+    n = A.shape[0]
+    d = np.abs(A.diagonal())
+    absA = abs(A)
+    S = 0.5 * (absA + absA.T)          # (|a_ij| + |a_ji|) / 2
+    S = S.tocoo()
+    keep = (S.row != S.col) & (S.data >= theta * np.sqrt(d[S.row] * d[S.col]))
+    G = sp.csr_matrix((np.ones(int(keep.sum()), dtype=np.int8),
+                       (S.row[keep], S.col[keep])), shape=(n, n))
+    G.sort_indices()
+    return G
+
+
+def mis2_roots(G: sp.csr_matrix, level: int) -> np.ndarray:
+    """Greedy maximal distance-2 independent set in decreasing priority."""
+    n = G.shape[0]
+    key = priority_keys(n, level)
+    order = np.argsort(key)[::-1]
+    ip, ix = G.indptr, G.indices
+    UND, ROOT, OUT = 0, 1, 2
+    state = np.zeros(n, dtype=np.int8)
+    for v in order:
+        if state[v] != UND:
+            continue
+        state[v] = ROOT
+        nb1 = ix[ip[v]:ip[v + 1]]
+        for u in nb1:
+            if state[u] == UND:
+                state[u] = OUT
+            for w in ix[ip[u]:ip[u + 1]]:
+                if state[w] == UND:
+                    state[w] = OUT
+    return state == ROOT
+
+
+def aggregate(G: sp.csr_matrix, level: int):
+    """Aggregate index per node (0..nc-1) and the root mask."""
+    n = G.shape[0]
+    root = mis2_roots(G, level)
+    key = priority_keys(n, level)
+    agg = np.full(n, -1, dtype=np.int64)
+    roots = np.flatnonzero(root)
+    agg[roots] = np.arange(roots.size)
+    ip, ix = G.indptr, G.indices
+    phase1 = agg.copy()
+    for r in roots:
+        for u in ix[ip[r]:ip[r + 1]]:
+            phase1[u] = agg[r]
+    agg = phase1.copy()
+    for v in np.flatnonzero(phase1 < 0):
+        nb = ix[ip[v]:ip[v + 1]]
+        cand = nb[phase1[nb] >= 0]
+        if cand.size == 0:
+            raise RuntimeError("node without an aggregated strong neighbour")
+        u = cand[np.argmax(key[cand])]
+        agg[v] = phase1[u]
+    return agg, root
+
+
+def smoothed_prolongator(A: sp.csr_matrix, agg: np.ndarray, nc: int):
+    n = A.shape[0]
+    Pt = sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, nc))
+    diag = A.diagonal()
+    rho = np.max(np.asarray(abs(A).sum(axis=1)).ravel() / np.abs(diag))
+    omega = 4.0 / (3.0 * rho)
+    Dinv = sp.diags(1.0 / diag)
+    P = (Pt - omega * (Dinv @ (A @ Pt))).tocsr()
+    P.sort_indices()
+    return P, omega
+
+
+class Level:
+    def __init__(self, A):
+        self.A = A.tocsr()
+        self.A.sort_indices()
+        self.n = A.shape[0]
+        self.dl1 = np.asarray(abs(self.A).sum(axis=1)).ravel()
+        self.P = None
+        self.R = None
+        self.agg = None
+        self.lu = None
+
+
+class Hierarchy:
+    """AMG hierarchy of one diagonal block."""
+
+    def __init__(self, A, theta=0.08, coarse_max=256, max_levels=12,
+                 nu_pre=1, nu_post=1, smoother="chebyshev", cheb_degree=3,
+                 cheb_lo=0.1):
+        self.theta = theta
+        self.nu_pre = nu_pre
+        self.nu_post = nu_post
+        if smoother not in ("l1jacobi", "chebyshev"):
+            raise ValueError(smoother)
+        self.smoother = smoother
+        self.cheb_degree = cheb_degree
+        self.cheb_lo = cheb_lo
+        self.levels = [Level(A)]
+        while True:
+            lev = self.levels[-1]
+            lvl = len(self.levels) - 1
+            if lev.n <= coarse_max or len(self.levels) >= max_levels:
+                break
+            G = strength_graph(lev.A, theta)
+            agg, _ = aggregate(G, lvl)
+            nc = int(agg.max()) + 1
+            if nc >= lev.n:
+                break
+            P, _ = smoothed_prolongator(lev.A, agg, nc)
+            lev.P = P
+            lev.R = P.T.tocsr()
+            lev.agg = agg
+            Ac = (lev.R @ lev.A @ P).tocsr()
+            self.levels.append(Level(Ac))
+        last = self.levels[-1]
+        last.lu = sla.lu_factor(last.A.toarray())
+
+    def sizes(self):
+        return [lev.n for lev in self.levels]
+
+    def smooth(self, lev, b, x):
+        """One smoothing sweep on level ``lev``."""
+        if self.smoother == "l1jacobi":
+            return x + (b - lev.A @ x) / lev.dl1
+        lo = self.cheb_lo
+        theta = 0.5 * (1.0 + lo)
+        delta = 0.5 * (1.0 - lo)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        d = ((b - lev.A @ x) / lev.dl1) / theta
+        x = x + d
+        for _ in range(1, self.cheb_degree):
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            d = rho_new * rho * d + (2.0 * rho_new / delta) * ((b - lev.A @ x) / lev.dl1)
+            x = x + d
+            rho = rho_new
+        return x
+
+    def vcycle(self, b, l=0):
+        lev = self.levels[l]
+        if lev.lu is not None:
+            return sla.lu_solve(lev.lu, b)
+        x = np.zeros_like(b)
+        for _ in range(self.nu_pre):
+            x = self.smooth(lev, b, x)
+        r = b - lev.A @ x
+        e = self.vcycle(lev.R @ r, l + 1)
+        x = x + lev.P @ e
+        for _ in range(self.nu_post):
+            x = self.smooth(lev, b, x)
+        return x

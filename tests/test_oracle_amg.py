@@ -1,0 +1,140 @@
+"""Pins for oracle/amg.py: the hash, the distance-2 independent set, the
+aggregation rule, the Galerkin product, and the V-cycle as a linear,
+convergent operator."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import amg
+from oracle import butcher as bt
+from oracle import fem
+
+
+def _block(N, c=0.05 * 0.4, domain="unit", eps=None):
+    mesh = synth.structured_mesh(N, domain)
+    if eps is None:
+        prob = fem.heat_problem(mesh)
+    else:
+        prob = fem.double_glazing_problem(mesh, eps, synth.double_glazing_wind,
+                                          synth.double_glazing_boundary(mesh))
+    return (prob.M + c * prob.F).tocsr()
+
+
+def test_fmix32_reference_values():
+    # MurmurHash3 fmix32: fmix32(0) = 0, and the bijection is invertible
+    assert amg.fmix32(0) == 0
+    vals = [amg.fmix32(i) for i in range(1 << 12)]
+    assert len(set(vals)) == len(vals)
+    k = amg.priority_keys(5000, 2)
+    assert np.all((k >> np.uint64(32)) == np.array([amg.fmix32(i ^ ((0x9E3779B9 * 3) & 0xFFFFFFFF))
+                                                   for i in range(5000)], dtype=np.uint64))
+    assert len(np.unique(k)) == 5000
+
+
+def _dist2(G):
+    G = G.astype(np.int32)
+    I = sp.identity(G.shape[0], dtype=np.int32, format="csr")
+    return ((I + G) @ (I + G)).tocsr()
+
+
+@pytest.mark.parametrize("eps", [None, 0.005])
+def test_mis2_independent_maximal(eps):
+    A = _block(24, domain="unit" if eps is None else "box", eps=eps)
+    G = amg.strength_graph(A, 0.08)
+    assert abs(G - G.T).max() == 0
+    root = amg.mis2_roots(G, 0)
+    D2 = _dist2(G)
+    r = np.flatnonzero(root)
+    # independent: no two roots within distance 2
+    sub = D2[r][:, r]
+    assert sub.nnz == r.size
+    # maximal: every node is within distance 2 of a root
+    cover = D2[:, r].sum(axis=1).A.ravel()
+    assert np.all(cover > 0)
+
+
+def test_mis2_equals_parallel_rounds():
+    """The greedy set equals the fixed-priority parallel rounds (select the
+    undecided nodes whose key is the maximum over undecided nodes within
+    distance 2; drop nodes within distance 2 of a root; repeat)."""
+    A = _block(30)
+    G = amg.strength_graph(A, 0.08)
+    n = A.shape[0]
+    key = amg.priority_keys(n, 1)
+    D2 = _dist2(G)
+    state = np.zeros(n, dtype=np.int8)   # 0 undecided, 1 root, 2 out
+    while np.any(state == 0):
+        und = state == 0
+        kk = np.where(und, key, np.uint64(0))
+        new = state.copy()
+        for v in np.flatnonzero(und):
+            nb = D2.indices[D2.indptr[v]:D2.indptr[v + 1]]
+            if np.any(state[nb] == 1):
+                new[v] = 2
+            elif kk[nb].max() == key[v]:
+                new[v] = 1
+        state = new
+    assert np.array_equal(state == 1, amg.mis2_roots(G, 1))
+
+
+def test_aggregates_partition():
+    A = _block(40)
+    G = amg.strength_graph(A, 0.08)
+    agg, root = amg.aggregate(G, 0)
+    nc = agg.max() + 1
+    assert agg.min() == 0 and np.unique(agg).size == nc == root.sum()
+    # numbering by increasing root index
+    assert np.array_equal(agg[np.flatnonzero(root)], np.arange(nc))
+    # each aggregate is connected in the strength graph and contains its root
+    for a in range(0, nc, 7):
+        members = np.flatnonzero(agg == a)
+        sub = G[members][:, members]
+        ncomp, _ = sp.csgraph.connected_components(sub, directed=False)
+        assert ncomp == 1
+    sizes = np.bincount(agg)
+    assert 4 <= sizes.mean() <= 16
+
+
+def test_galerkin_and_hierarchy():
+    A = _block(48)
+    H = amg.Hierarchy(A, coarse_max=64)
+    assert len(H.levels) >= 3
+    for l in range(len(H.levels) - 1):
+        lev, nxt = H.levels[l], H.levels[l + 1]
+        Pd = lev.P.toarray()
+        Ad = lev.A.toarray()
+        assert np.allclose(nxt.A.toarray(), Pd.T @ Ad @ Pd, atol=1e-13 * np.abs(Ad).max())
+        # P reproduces the smoothed constant: row sums of P_t are one
+        assert np.allclose(np.asarray((lev.R.T - lev.P).sum()), 0)
+    assert H.levels[-1].n <= 64
+
+
+def test_vcycle_linear_and_convergent():
+    A = _block(64)
+    H = amg.Hierarchy(A)
+    rng = np.random.default_rng(0)
+    b1 = rng.standard_normal(A.shape[0])
+    b2 = rng.standard_normal(A.shape[0])
+    v = H.vcycle(2.0 * b1 - 3.0 * b2)
+    assert np.allclose(v, 2.0 * H.vcycle(b1) - 3.0 * H.vcycle(b2), atol=1e-12)
+    # stationary iteration x <- x + V(b - A x): contraction factor
+    x = np.zeros_like(b1)
+    r0 = np.linalg.norm(b1)
+    for _ in range(8):
+        x = x + H.vcycle(b1 - A @ x)
+    rate = (np.linalg.norm(b1 - A @ x) / r0) ** (1 / 8)
+    assert rate < 0.5, rate
+
+
+def test_vcycle_nonsymmetric_block():
+    # double-glazing block (eps = 1/200, h = 0.01 * d_jj): still a contraction
+    A, _, _ = bt.radau_iia(3)
+    _, D, _ = bt.ldu(A)
+    Bk = _block(64, c=0.01 * D[0, 0], domain="box", eps=1 / 200)
+    H = amg.Hierarchy(Bk)
+    b = np.random.default_rng(2).standard_normal(Bk.shape[0])
+    x = np.zeros_like(b)
+    for _ in range(10):
+        x = x + H.vcycle(b - Bk @ x)
+    assert np.linalg.norm(b - Bk @ x) < 1e-2 * np.linalg.norm(b)

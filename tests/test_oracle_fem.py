@@ -1,0 +1,88 @@
+"""Pins for oracle/fem.py: exact integrals of polynomials, null spaces and
+skew-symmetry of the P1 matrices of Section 3."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem
+
+
+@pytest.mark.parametrize("N,domain", [(4, "unit"), (7, "box")])
+def test_mass_and_stiffness_exact(N, domain):
+    mesh = synth.structured_mesh(N, domain)
+    mats = fem.assemble(mesh.xy, mesh.tri)
+    M, K = mats["M"], mats["K"]
+    area = (mesh.hi[0] - mesh.lo[0]) * (mesh.hi[1] - mesh.lo[1])
+    one = np.ones(mesh.n_nodes)
+    assert abs(one @ M @ one - area) < 1e-13 * area
+    assert np.max(np.abs(K @ one)) < 1e-12
+    assert abs(M - M.T).max() < 1e-16 and abs(K - K.T).max() < 1e-14
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    # linear u = 2x - 3y + 1: int |grad u|^2 = 13 * area; int u^2 exact (P1 interp exact)
+    u = 2 * x - 3 * y + 1
+    assert abs(u @ K @ u - 13.0 * area) < 1e-11
+    (x0, y0), (x1, y1) = mesh.lo, mesh.hi
+    # int (2x - 3y + 1)^2 over the rectangle, by hand
+    def I(px, py):
+        return (x1 ** (px + 1) - x0 ** (px + 1)) / (px + 1) * (y1 ** (py + 1) - y0 ** (py + 1)) / (py + 1)
+    exact = 4 * I(2, 0) + 9 * I(0, 2) + I(0, 0) - 12 * I(1, 1) + 4 * I(1, 0) - 6 * I(0, 1)
+    assert abs(u @ M @ u - exact) < 1e-12
+
+
+def test_stiffness_stencil_uniform():
+    # interior row of the uniform right-triangle mesh: 4 on the diagonal, -1 at
+    # the four axis neighbours, 0 at the two diagonal neighbours
+    mesh = synth.structured_mesh(6)
+    K = fem.assemble(mesh.xy, mesh.tri)["K"].tocsr()
+    i = 3 * 7 + 3
+    row = dict(zip(K.indices[K.indptr[i]:K.indptr[i + 1]], K.data[K.indptr[i]:K.indptr[i + 1]]))
+    assert abs(row[i] - 4) < 1e-14
+    for j in (i - 1, i + 1, i - 7, i + 7):
+        assert abs(row[j] + 1) < 1e-14
+    for j in (i - 8, i + 8):
+        assert abs(row[j]) < 1e-14
+    assert len(row) == 7
+
+
+def test_convection_double_glazing():
+    """C_kl = int phi_k (w . grad phi_l) with w = (2y(1-x^2), -2x(1-y^2)):
+    div w = 0 and w.n = 0 on the box boundary give C + C^T = 0; C 1 = 0; and
+    v^T C u = int v (w . grad u) for linear u, v (exact with the rule):
+    v = y, u = x -> 16/9;  v = x, u = y -> -16/9."""
+    mesh = synth.structured_mesh(8, "box")
+    C = fem.assemble(mesh.xy, mesh.tri, wind=synth.double_glazing_wind)["C"]
+    assert abs(C + C.T).max() < 1e-15
+    assert np.max(np.abs(C @ np.ones(mesh.n_nodes))) < 1e-15
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    assert abs(y @ C @ x - 16 / 9) < 1e-13
+    assert abs(x @ C @ y + 16 / 9) < 1e-13
+
+
+def test_kappa_linearity():
+    mesh = synth.structured_mesh(5)
+    rng = np.random.default_rng(3)
+    kap = np.exp(rng.standard_normal(mesh.n_tri))
+    K = fem.assemble(mesh.xy, mesh.tri, kappa=kap)["K"].toarray()
+    Ke = fem.element_stiffness_unit(mesh.xy, mesh.tri)
+    K2 = np.zeros_like(K)
+    for e in range(mesh.n_tri):
+        t = mesh.tri[e]
+        K2[np.ix_(t, t)] += kap[e] * Ke[e]
+    assert np.max(np.abs(K - K2)) < 1e-13
+
+
+def test_problem_restriction():
+    mesh = synth.structured_mesh(6, "box")
+    ub = synth.double_glazing_boundary(mesh)
+    prob = fem.double_glazing_problem(mesh, 0.005, synth.double_glazing_wind, ub)
+    assert prob.M.shape == (25, 25) and prob.F.shape == (25, 25)
+    # lift: F_full @ u_full restricted to interior rows equals F_II u_I + g
+    mats = fem.assemble(mesh.xy, mesh.tri, wind=synth.double_glazing_wind)
+    Ff = (0.005 * mats["K"] + mats["C"]).tocsr()
+    uI = np.random.default_rng(0).standard_normal(mesh.n)
+    full = ub.copy()
+    full[mesh.interior] = uI
+    assert np.allclose((Ff @ full)[mesh.interior], prob.F @ uI + prob.g, atol=1e-14)
+    # hot east wall only
+    east = mesh.xy[:, 0] == 1.0
+    assert np.all(ub[east] == 1) and np.all(ub[~east] == 0)

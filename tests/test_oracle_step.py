@@ -1,0 +1,184 @@
+"""Pins for oracle/irk.py: the IRK step against its closed form, temporal
+order, the spectral identity of the preconditioned Kronecker system, the
+substitutions of Section 4.2 against dense solves, and FGMRES."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import synth
+from oracle import butcher as bt
+from oracle import fem
+from oracle import irk
+
+
+def _heat(N):
+    mesh = synth.structured_mesh(N)
+    return mesh, fem.heat_problem(mesh)
+
+
+def _closed_form_step(prob, A, b, h, u):
+    """u_{n+1} = V R(-h Lambda) V^{-1} u_n with F V = M V Lambda (M-orthonormal V)."""
+    lam, V = sla.eigh(prob.F.toarray(), prob.M.toarray())
+    R = np.array([bt.stability_function(A, b, -h * l) for l in lam])
+    return V @ (R * (V.T @ (prob.M @ u)))
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5])
+def test_step_closed_form(s):
+    mesh, prob = _heat(7)
+    A, b, _ = bt.radau_iia(s)
+    h = 0.05
+    u = synth.heat_u0(mesh)
+    sol = irk.IRKSolver(prob, A, b, h, kind=None)
+    r = sol.step(u, direct=True)
+    ref = _closed_form_step(prob, A, b, h, u)
+    assert np.linalg.norm(r.u - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_step_closed_form_lobatto_dg():
+    # nonsymmetric F (double glazing): compare with the dense matrix function
+    mesh = synth.structured_mesh(6, "box")
+    ub = synth.double_glazing_boundary(mesh)
+    prob = fem.double_glazing_problem(mesh, 0.02, synth.double_glazing_wind, ub)
+    A, b, _ = bt.lobatto_iiic(3)
+    h = 0.01
+    u = np.random.default_rng(1).standard_normal(prob.n)
+    sol = irk.IRKSolver(prob, A, b, h, kind=None)
+    r = sol.step(u, direct=True)
+    # u' = -M^{-1}(F u + g): stage values K_i = -M^{-1}(F(u + h sum a_ij K_j) + g)
+    Mi = np.linalg.inv(prob.M.toarray())
+    J = -Mi @ prob.F.toarray()
+    f0 = -Mi @ prob.g
+    s = A.shape[0]
+    n = prob.n
+    big = np.eye(s * n) - h * np.kron(A, J)
+    rhs = np.tile(J @ u + f0, s)
+    K = np.linalg.solve(big, rhs).reshape(s, n)
+    ref = u + h * b @ K
+    assert np.linalg.norm(r.u - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_temporal_order(s):
+    """Against the semi-discrete exact solution exp(-t M^{-1} F) u0 the error
+    falls like h^(2s-1) (Table 1 order of Radau IIA)."""
+    mesh, prob = _heat(6)
+    A, b, _ = bt.radau_iia(s)
+    u0 = synth.heat_u0(mesh)
+    lam, V = sla.eigh(prob.F.toarray(), prob.M.toarray())
+    T = 0.2
+    exact = V @ (np.exp(-T * lam) * (V.T @ (prob.M @ u0)))
+    errs = []
+    for nst in (4, 8, 16):
+        sol = irk.IRKSolver(prob, A, b, T / nst, kind=None)
+        us, _ = sol.run(u0, nst, direct=True)
+        errs.append(np.linalg.norm(us[-1] - exact))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > (2 * s - 1) - 0.35), rates
+
+
+def test_operator_matches_kron():
+    mesh, prob = _heat(5)
+    A, _, _ = bt.radau_iia(3)
+    h = 0.1
+    z = synth.random_stage_block(prob.n, 3, 0)
+    K = irk.kron_matrix(prob.M, prob.F, A, h)
+    w1 = irk.apply_operator(prob.M, prob.F, A, h, z)
+    w2 = (K @ z.ravel()).reshape(z.shape)
+    assert np.allclose(w1, w2, atol=1e-14, rtol=0)
+
+
+@pytest.mark.parametrize("kind", ["J", "GSL", "GSL_OPT", "DU", "LD"])
+def test_preconditioner_substitution_is_exact(kind):
+    """Section 4.2: the substitution with exact subsolves equals a dense solve
+    with P = I (x) M + h A~ (x) F (both directions, and the transpose)."""
+    mesh, prob = _heat(5)
+    A, _, _ = bt.radau_iia(4)
+    h = 0.07
+    v = synth.random_stage_block(prob.n, 4, 1)
+    At0 = None
+    for transpose in (False, True):
+        pc = irk.BlockPreconditioner(prob.M, prob.F, A, h, kind, "direct", transpose=transpose)
+        if At0 is None:
+            At0 = pc.At.copy()
+            if kind != "GSL_OPT":
+                assert np.array_equal(At0, bt.atilde(A, kind))
+        At = At0.T if transpose else At0
+        assert np.array_equal(pc.At, At)
+        P = irk.kron_matrix(prob.M, prob.F, At, h).toarray()
+        ref = np.linalg.solve(P, v.ravel()).reshape(v.shape)
+        w = pc.apply(v)
+        assert np.max(np.abs(w - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_spectral_identity():
+    """eig(P^{-1} A) = U_lambda eig((I + h lam A~)^{-1}(I + h lam A)) over the
+    generalised eigenvalues lam of (F, M): brute force on a tiny mesh."""
+    mesh, prob = _heat(4)
+    A, _, _ = bt.radau_iia(3)
+    h = 0.05
+    lam = sla.eigh(prob.F.toarray(), prob.M.toarray(), eigvals_only=True)
+    for kind in ("J", "GSL", "DU", "LD"):
+        At = bt.atilde(A, kind)
+        Kd = irk.kron_matrix(prob.M, prob.F, A, h).toarray()
+        Pd = irk.kron_matrix(prob.M, prob.F, At, h).toarray()
+        brute = np.sort_complex(np.linalg.eigvals(np.linalg.solve(Pd, Kd)))
+        small = []
+        for l in lam:
+            small.extend(np.linalg.eigvals(np.linalg.solve(np.eye(3) + h * l * At,
+                                                           np.eye(3) + h * l * A)))
+        small = np.sort_complex(np.array(small))
+        assert np.max(np.abs(brute - small)) < 1e-10
+
+
+@pytest.mark.parametrize("kind", ["J", "GSL", "DU", "LD"])
+def test_fgmres_mms(kind):
+    """Manufactured solution (Section 5): r = A k*, solve to rtol 1e-10."""
+    mesh, prob = _heat(12)
+    A, b, _ = bt.radau_iia(3)
+    h = 0.05
+    kstar = synth.random_stage_block(prob.n, 3, 7)
+    sol = irk.IRKSolver(prob, A, b, h, kind=kind, subsolve="amg")
+    rhs = sol.op(kstar)
+    res = sol.solve_stages(rhs)
+    assert res.converged
+    assert np.linalg.norm(sol.op(res.x) - rhs) <= 1e-10 * np.linalg.norm(rhs)
+    assert np.linalg.norm(res.x - kstar) <= 1e-7 * np.linalg.norm(kstar)
+
+
+def test_exact_preconditioner_one_iteration():
+    """A~ = A with exact subsolves makes P = A: one FGMRES iteration; and
+    s = 1 makes every preconditioner exact."""
+    mesh, prob = _heat(8)
+    A, b, _ = bt.radau_iia(3)
+    sol = irk.IRKSolver(prob, A, b, 0.05, kind="LD", subsolve="direct",
+                        Atilde=A.copy())
+    # the FULL coefficient matrix is not triangular: apply P^{-1} densely
+    P = irk.kron_matrix(prob.M, prob.F, A, 0.05)
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(P)
+    rhs = irk.stage_rhs(prob.F, prob.g, synth.heat_u0(mesh), 3)
+    res = irk.fgmres(sol.op, lambda v: lu.solve(v.ravel()).reshape(v.shape), rhs)
+    assert res.iterations == 1
+    A1, b1, _ = bt.radau_iia(1)
+    for kind in ("J", "GSL", "DU", "LD"):
+        s1 = irk.IRKSolver(prob, A1, b1, 0.05, kind=kind, subsolve="direct")
+        r = s1.step(synth.heat_u0(mesh))
+        assert r.iterations == 1
+
+
+def test_fgmres_direct_subsolve_counts_c1():
+    """32^2 heat, Radau IIA s=2, h=0.05, step 1 with exact subsolves: LD needs
+    the fewest iterations and J the most (the ordering of Table 5)."""
+    mesh, prob = _heat(32)
+    A, b, _ = bt.radau_iia(2)
+    its = {}
+    for kind in ("J", "GSL", "DU", "LD"):
+        sol = irk.IRKSolver(prob, A, b, 0.05, kind=kind, subsolve="direct")
+        its[kind] = sol.step(synth.heat_u0(mesh)).iterations
+    assert its["J"] > its["GSL"] >= its["LD"]
+    assert its["J"] > its["DU"] >= its["LD"]
+    direct = irk.IRKSolver(prob, A, b, 0.05, kind=None).step(synth.heat_u0(mesh), direct=True).u
+    sol = irk.IRKSolver(prob, A, b, 0.05, kind="LD", subsolve="amg")
+    st = sol.step(synth.heat_u0(mesh))
+    assert np.linalg.norm(st.u - direct) <= 1e-9 * np.linalg.norm(direct)
