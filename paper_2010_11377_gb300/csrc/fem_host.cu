@@ -1,0 +1,182 @@
+// Host P1 assembly of the interior-unknown matrices of Section 3:
+//   M_kl = int phi_k phi_l,  F = sum_e kappa_e K_e + C,
+//   K_e[a,b] = |T| grad l_a . grad l_b,  C_kl = int phi_k (w . grad phi_l),
+// with strong Dirichlet elimination and the lift g = F_IB u_B.  The convection
+// integrand (P1 times the sampled wind) uses the symmetric 6-point degree-4
+// rule of Dunavant (1985); callers sample the wind at irk_fem_quad_points.
+#include "irk_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace {
+
+// barycentric coordinates and weights (weights sum to 1) of the degree-4 rule
+const double kA1 = 0.445948490915965, kW1 = 0.223381589678011;
+const double kA2 = 0.091576213509771, kW2 = 0.109951743655322;
+
+void rule(double bary[6][3], double w[6]) {
+  const double a[2] = {kA1, kA2}, ww[2] = {kW1, kW2};
+  int q = 0;
+  for (int g = 0; g < 2; ++g) {
+    double x = a[g], y = 1.0 - 2.0 * a[g];
+    double pts[3][3] = {{x, x, y}, {x, y, x}, {y, x, x}};
+    for (int k = 0; k < 3; ++k, ++q) {
+      bary[q][0] = pts[k][0];
+      bary[q][1] = pts[k][1];
+      bary[q][2] = pts[k][2];
+      w[q] = ww[g];
+    }
+  }
+}
+
+struct Geo {
+  double area;
+  double gx[3], gy[3];
+};
+
+bool geometry(const double* xy, const int32_t* t, Geo& g) {
+  double x0 = xy[2 * t[0]], y0 = xy[2 * t[0] + 1];
+  double x1 = xy[2 * t[1]], y1 = xy[2 * t[1] + 1];
+  double x2 = xy[2 * t[2]], y2 = xy[2 * t[2] + 1];
+  double det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+  if (!(det > 0.0)) return false;
+  g.area = 0.5 * det;
+  g.gx[0] = (y1 - y2) / det;
+  g.gx[1] = (y2 - y0) / det;
+  g.gx[2] = (y0 - y1) / det;
+  g.gy[0] = (x2 - x1) / det;
+  g.gy[1] = (x0 - x2) / det;
+  g.gy[2] = (x1 - x0) / det;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+irk_status irk_fem_quad_points(int32_t n_tri, const double* xy, const int32_t* tri, double* xq) {
+  if (n_tri < 0 || (n_tri > 0 && (!xy || !tri || !xq))) {
+    irk::set_global_error("bad argument to irk_fem_quad_points");
+    return IRK_ERR_INVALID;
+  }
+  double bary[6][3], w[6];
+  rule(bary, w);
+  for (int e = 0; e < n_tri; ++e) {
+    const int32_t* t = tri + 3 * e;
+    for (int q = 0; q < 6; ++q) {
+      double x = 0.0, y = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        x += bary[q][a] * xy[2 * t[a]];
+        y += bary[q][a] * xy[2 * t[a] + 1];
+      }
+      xq[(size_t(e) * 6 + q) * 2] = x;
+      xq[(size_t(e) * 6 + q) * 2 + 1] = y;
+    }
+  }
+  return IRK_OK;
+}
+
+irk_status irk_fem_assemble(int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri, const int32_t* dof,
+                            int32_t n, const double* kappa, const double* wind, const double* ub, int64_t* nnz,
+                            int64_t* rowptr, int32_t* col, double* valM, double* valF, double* g) {
+  if (n_nodes <= 0 || n_tri <= 0 || n <= 0 || !xy || !tri || !dof || !nnz) {
+    irk::set_global_error("bad argument to irk_fem_assemble");
+    return IRK_ERR_INVALID;
+  }
+  for (int e = 0; e < 3 * n_tri; ++e)
+    if (tri[e] < 0 || tri[e] >= n_nodes) {
+      irk::set_global_error("triangle vertex out of range");
+      return IRK_ERR_INVALID;
+    }
+  for (int v = 0; v < n_nodes; ++v)
+    if (dof[v] >= n) {
+      irk::set_global_error("dof index out of range");
+      return IRK_ERR_INVALID;
+    }
+  // pattern: interior couplings of each element, sorted and unique per row
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (int e = 0; e < n_tri; ++e)
+    for (int a = 0; a < 3; ++a) {
+      int da = dof[tri[3 * e + a]];
+      if (da < 0) continue;
+      for (int b = 0; b < 3; ++b)
+        if (dof[tri[3 * e + b]] >= 0) ++cnt[da + 1];
+    }
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> raw(cnt[n]);
+  std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
+  for (int e = 0; e < n_tri; ++e)
+    for (int a = 0; a < 3; ++a) {
+      int da = dof[tri[3 * e + a]];
+      if (da < 0) continue;
+      for (int b = 0; b < 3; ++b) {
+        int db = dof[tri[3 * e + b]];
+        if (db >= 0) raw[cur[da]++] = db;
+      }
+    }
+  std::vector<int64_t> rp(n + 1, 0);
+  std::vector<int> cl;
+  cl.reserve(raw.size() / 2 + 1);
+  for (int i = 0; i < n; ++i) {
+    auto b = raw.begin() + cnt[i], e = raw.begin() + cnt[i + 1];
+    std::sort(b, e);
+    auto u = std::unique(b, e);
+    cl.insert(cl.end(), b, u);
+    rp[i + 1] = static_cast<int64_t>(cl.size());
+  }
+  *nnz = rp[n];
+  if (!rowptr || !col || !valM || !valF) return IRK_OK;   // size query
+  std::copy(rp.begin(), rp.end(), rowptr);
+  std::copy(cl.begin(), cl.end(), col);
+  std::fill(valM, valM + rp[n], 0.0);
+  std::fill(valF, valF + rp[n], 0.0);
+  if (g) std::fill(g, g + n, 0.0);
+  double bary[6][3], w[6];
+  rule(bary, w);
+  for (int e = 0; e < n_tri; ++e) {
+    const int32_t* t = tri + 3 * e;
+    Geo geo;
+    if (!geometry(xy, t, geo)) {
+      irk::set_global_error("mesh triangles must be counter-clockwise and non-degenerate");
+      return IRK_ERR_INVALID;
+    }
+    double ke = kappa ? kappa[e] : 1.0;
+    double Me[3][3], Fe[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        Me[a][b] = geo.area / 12.0 * (a == b ? 2.0 : 1.0);
+        Fe[a][b] = ke * geo.area * (geo.gx[a] * geo.gx[b] + geo.gy[a] * geo.gy[b]);
+      }
+    if (wind) {
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double s = 0.0;
+          for (int q = 0; q < 6; ++q) {
+            double wx = wind[(size_t(e) * 6 + q) * 2], wy = wind[(size_t(e) * 6 + q) * 2 + 1];
+            s += w[q] * bary[q][a] * (wx * geo.gx[b] + wy * geo.gy[b]);
+          }
+          Fe[a][b] += geo.area * s;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+      int da = dof[t[a]];
+      if (da < 0) continue;
+      for (int b = 0; b < 3; ++b) {
+        int db = dof[t[b]];
+        if (db < 0) {
+          if (g && ub) g[da] += Fe[a][b] * ub[t[b]];
+          continue;
+        }
+        auto beg = cl.begin() + rp[da], end = cl.begin() + rp[da + 1];
+        int64_t pos = std::lower_bound(beg, end, db) - cl.begin();
+        valM[pos] += Me[a][b];
+        valF[pos] += Fe[a][b];
+      }
+    }
+  }
+  return IRK_OK;
+}
+
+}  // extern "C"

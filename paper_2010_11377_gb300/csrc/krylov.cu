@@ -1,0 +1,654 @@
+// FP64 kernels of the outer solve: the Kronecker operator of Section 4,
+// A z = (I_s (x) M + h A (x) F) z, the stage right-hand side of
+// Eq. block_coeff_mtx, restarted right-preconditioned flexible GMRES with
+// classical Gram-Schmidt (reorthogonalised when the projected norm drops below
+// 1/sqrt(2) of the original), the IRK update u_{n+1} = u_n + h sum_i b_i k_i
+// (Section 2), and the discrete adjoint kernels.
+//
+// All FGMRES control lives on the device (GmresState): the index j, the
+// Hessenberg matrix, the Givens rotations and the convergence decision, so an
+// iteration is a fixed kernel sequence that a CUDA graph replays.  Reductions
+// are deterministic: per-block partial sums (fixed shuffle tree), then the
+// last block to finish sums the partials in block order.
+#include "irk_internal.cuh"
+
+#include <cmath>
+
+namespace irk {
+
+constexpr int PL = MAX_M + 2;   // partial-sum slots per block
+constexpr int BS = 256;         // threads per block of the outer kernels
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+// sum NV per-thread values over the block; thread t < NV writes slot t
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* __restrict__ out, int cnt = NV) {
+  __shared__ double sm[BS / 32][NV];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[q] = x;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sm[warp][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV && threadIdx.x < cnt) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < BS / 32; ++w) s += sm[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool last_block(GmresState* st) {
+  __shared__ bool am;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(&st->counter, 1u);
+    am = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return am;
+}
+
+// total of slot q over all blocks, in block order
+__device__ __forceinline__ double gather_partials(const double* partials, int q) {
+  double s = 0.0;
+  for (int b = 0; b < static_cast<int>(gridDim.x); ++b) s += ldcg(partials + int64_t(b) * PL + q);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Givens update of Hessenberg column j and the convergence decision
+// ---------------------------------------------------------------------------
+__device__ void gmres_finish(GmresState* st, double hnext) {
+  int j = st->j;
+  double* Hc = st->H + j * (MAX_M + 1);
+  Hc[j + 1] = hnext;
+  st->sigma[j + 1] = (hnext != 0.0) ? 1.0 / hnext : 0.0;
+  for (int i = 0; i < j; ++i) {
+    double t = st->cs[i] * Hc[i] + st->sn[i] * Hc[i + 1];
+    Hc[i + 1] = -st->sn[i] * Hc[i] + st->cs[i] * Hc[i + 1];
+    Hc[i] = t;
+  }
+  double den = hypot(Hc[j], Hc[j + 1]);
+  double c = den != 0.0 ? Hc[j] / den : 1.0;
+  double s = den != 0.0 ? Hc[j + 1] / den : 0.0;
+  st->cs[j] = c;
+  st->sn[j] = s;
+  Hc[j] = den;
+  Hc[j + 1] = 0.0;
+  st->g[j + 1] = -s * st->g[j];
+  st->g[j] = c * st->g[j];
+  st->it += 1;
+  double est = fabs(st->g[j + 1]);
+  bool bad = !isfinite(est) || !isfinite(den);
+  if (bad) {
+    st->status = IRK_ERR_NONFINITE;
+    st->done = 1;
+    return;
+  }
+  bool conv = est <= st->rtol * st->bnorm;
+  if (conv || j + 1 >= st->m || st->it >= st->max_it || hnext == 0.0 || den == 0.0)
+    st->cycle_end = 1;
+  else
+    st->j = j + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Kronecker operator, one thread per row (grid-stride), each nonzero of the
+// shared M/F pattern read once for all s stages:
+//   w_i = (M z_i) + sum_j (h a_ij) (F z_j)
+// MODE 0: w = A z;  MODE 1: w = b - A z with the squared norm reduced and the
+// restart decision taken by the last block (true residual of FGMRES).
+// ---------------------------------------------------------------------------
+template <int S, typename TZ, int MODE>
+__global__ void __launch_bounds__(BS)
+k_kron(int n, SellView<double> Mv, const double* __restrict__ Fval, JPtr<const TZ> zp, JPtr<double> wp,
+       KronCoef K, const double* __restrict__ bsub, GmresState* st, double* __restrict__ partials) {
+  if (st) {
+    if (st->done) return;
+    if (MODE == 1 && !st->cycle_end) return;
+  }
+  const TZ* __restrict__ z = zp.get();
+  double* __restrict__ w = wp.get();
+  double nrm = 0.0;
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    double mz[S], fz[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      mz[i] = 0.0;
+      fz[i] = 0.0;
+    }
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = Mv.sptr[sl];
+    int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
+    for (int k = 0; k < wdt; ++k) {
+      int64_t idx = base + (int64_t(k) << 5) + lane;
+      int c = Mv.col[idx];
+      double m = Mv.val[idx];
+      double f = Fval[idx];
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        double zz = static_cast<double>(z[int64_t(i) * n + c]);
+        mz[i] = fma(m, zz, mz[i]);
+        fz[i] = fma(f, zz, fz[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double wi = mz[i];
+#pragma unroll
+      for (int j = 0; j < S; ++j) wi = fma(K.a[i * MAX_S + j], fz[j], wi);
+      if (MODE == 1) {
+        wi = bsub[int64_t(i) * n + r] - wi;
+        nrm = fma(wi, wi, nrm);
+      }
+      w[int64_t(i) * n + r] = wi;
+    }
+  }
+  if (MODE == 1) {
+    double v[1] = {nrm};
+    block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
+    if (last_block(st)) {
+      if (threadIdx.x == 0) {
+        double beta = sqrt(gather_partials(partials, 0));
+        st->resid = beta / st->bnorm;
+        st->cycle_end = 0;
+        if (!isfinite(beta)) {
+          st->status = IRK_ERR_NONFINITE;
+          st->done = 1;
+        } else if (beta <= st->rtol * st->bnorm) {
+          st->done = 1;
+        } else if (st->it >= st->max_it) {
+          st->status = IRK_ERR_NOT_CONVERGED;
+          st->done = 1;
+        } else {
+          st->sigma[0] = 1.0 / beta;
+          st->g[0] = beta;
+          for (int i = 1; i <= MAX_M; ++i) st->g[i] = 0.0;
+          st->j = 0;
+          st->restarts += 1;
+        }
+        st->counter = 0;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram-Schmidt.  Basis vectors V_i are stored unnormalised; v_i = sigma_i V_i.
+// dots:  h_i = sigma_i <w, V_i> (i <= j) and ||w||^2 (PASS 0), or the
+//        reorthogonalisation coefficients (PASS 1, only when st->reorth).
+// axpy:  w -= sum_i h_i sigma_i V_i and ||w||^2; the last block decides on
+//        reorthogonalisation or finishes the iteration.
+// ---------------------------------------------------------------------------
+constexpr int CH = 16;
+
+template <int PASS>
+__global__ void __launch_bounds__(BS)
+k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, double* __restrict__ partials) {
+  if (st->done) return;
+  if (PASS == 1 && !st->reorth) return;
+  int j = st->j;
+  const double* __restrict__ w = V + int64_t(j + 1) * ldv;
+  int nvec = (PASS == 0) ? j + 2 : j + 1;   // PASS 0 also takes <w, w>
+  for (int i0 = 0; i0 < nvec; i0 += CH) {
+    double acc[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) acc[q] = 0.0;
+    int cnt = nvec - i0 < CH ? nvec - i0 : CH;
+    for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
+      double we = w[e];
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < cnt) acc[q] = fma(V[int64_t(i0 + q) * ldv + e], we, acc[q]);
+    }
+    block_sum_store<CH>(acc, partials + int64_t(blockIdx.x) * PL + i0, cnt);
+  }
+  if (last_block(st)) {
+    for (int i = threadIdx.x; i < nvec; i += BS) {
+      double d = gather_partials(partials, i);
+      if (i <= j) {
+        double h = st->sigma[i] * d;
+        if (PASS == 0) st->H[j * (MAX_M + 1) + i] = h;
+        else {
+          st->h2[i] = h;
+          st->H[j * (MAX_M + 1) + i] += h;
+        }
+      } else {
+        st->wnorm2 = d;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st->counter = 0;
+  }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(BS)
+k_gs_axpy(GmresState* st, double* __restrict__ V, int64_t ldv, int64_t N, double* __restrict__ partials) {
+  if (st->done) return;
+  if (PASS == 1 && !st->reorth) return;
+  __shared__ double coef[MAX_M + 1];
+  int j = st->j;
+  for (int i = threadIdx.x; i <= j; i += BS)
+    coef[i] = (PASS == 0 ? st->H[j * (MAX_M + 1) + i] : st->h2[i]) * st->sigma[i];
+  __syncthreads();
+  double* __restrict__ w = V + int64_t(j + 1) * ldv;
+  double nrm = 0.0;
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
+    double we = w[e];
+    int i = 0;
+    for (; i + 4 <= j + 1; i += 4) {
+      we = fma(-coef[i], V[int64_t(i) * ldv + e], we);
+      we = fma(-coef[i + 1], V[int64_t(i + 1) * ldv + e], we);
+      we = fma(-coef[i + 2], V[int64_t(i + 2) * ldv + e], we);
+      we = fma(-coef[i + 3], V[int64_t(i + 3) * ldv + e], we);
+    }
+    for (; i <= j; ++i) we = fma(-coef[i], V[int64_t(i) * ldv + e], we);
+    w[e] = we;
+    nrm = fma(we, we, nrm);
+  }
+  double v[1] = {nrm};
+  block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
+  if (last_block(st)) {
+    if (threadIdx.x == 0) {
+      double n2 = gather_partials(partials, 0);
+      if (PASS == 0 && (st->force_reorth || n2 < 0.5 * st->wnorm2)) {
+        st->reorth = 1;
+      } else {
+        st->reorth = 0;
+        gmres_finish(st, sqrt(n2));
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+// cycle end: y = H^{-1} g (upper triangular, k = j+1 columns; every block
+// solves it redundantly), then x += sum_i y_i Z_i
+template <typename TZ>
+__global__ void __launch_bounds__(BS)
+k_xupdate(GmresState* st, const TZ* __restrict__ Z, int64_t ldz, double* __restrict__ x, int64_t N) {
+  if (st->done || !st->cycle_end) return;
+  __shared__ double y[MAX_M];
+  int k = st->j + 1;
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = st->g[i];
+      for (int q = i + 1; q < k; ++q) s -= st->H[q * (MAX_M + 1) + i] * y[q];
+      y[i] = s / st->H[i * (MAX_M + 1) + i];
+    }
+  }
+  __syncthreads();
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
+    double xe = x[e];
+    for (int i = 0; i < k; ++i) xe = fma(y[i], static_cast<double>(Z[int64_t(i) * ldz + e]), xe);
+    x[e] = xe;
+  }
+}
+
+// WHILE-node condition: keep iterating until the solve is done.  The body
+// count is bounded independently of the solver logic: past max_it + 8 bodies
+// the solve stops with IRK_ERR_TIMEOUT.
+__global__ void k_loop_ctrl(GmresState* st, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->guard += 1;
+    if (!st->done && st->guard > st->max_it + 8) {
+      st->done = 1;
+      st->status = IRK_ERR_TIMEOUT;
+    }
+    cudaGraphSetConditional(h, st->done ? 0u : 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand sides and FGMRES initialisation (x = 0, V_0 = b, sigma_0 = 1/||b||)
+// ---------------------------------------------------------------------------
+__device__ void gmres_init_last(GmresState* st, double* partials, int m, int max_it, double rtol, int force) {
+  if (threadIdx.x == 0) {
+    double beta = sqrt(gather_partials(partials, 0));
+    st->bnorm = beta;
+    st->rtol = rtol;
+    st->m = m;
+    st->max_it = max_it;
+    st->force_reorth = force;
+    st->j = 0;
+    st->it = 0;
+    st->restarts = 0;
+    st->cycle_end = 0;
+    st->reorth = 0;
+    st->guard = 0;
+    st->status = IRK_OK;
+    st->resid = beta > 0.0 ? 1.0 : 0.0;
+    st->done = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+    if (!isfinite(beta)) st->status = IRK_ERR_NONFINITE;
+    st->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    st->g[0] = beta;
+    for (int i = 1; i <= MAX_M; ++i) st->g[i] = 0.0;
+    st->counter = 0;
+  }
+}
+
+// b_i = -(F u + g) for every stage (Eq. block_coeff_mtx); V_0 = b; x = 0
+template <int S>
+__global__ void __launch_bounds__(BS)
+k_rhs_forward(int n, SellView<double> Fv, const double* __restrict__ u, const double* __restrict__ g,
+              double* __restrict__ b, double* __restrict__ V0, double* __restrict__ x, GmresState* st,
+              double* __restrict__ partials, int m, int max_it, double rtol, int force) {
+  double nrm = 0.0;
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = Fv.sptr[sl];
+    int wdt = static_cast<int>((Fv.sptr[sl + 1] - base) >> 5);
+    double t = 0.0;
+    for (int k = 0; k < wdt; ++k) {
+      int64_t idx = base + (int64_t(k) << 5) + lane;
+      t = fma(Fv.val[idx], u[Fv.col[idx]], t);
+    }
+    t = -(t + (g ? g[r] : 0.0));
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      b[int64_t(i) * n + r] = t;
+      V0[int64_t(i) * n + r] = t;
+      x[int64_t(i) * n + r] = 0.0;
+      nrm = fma(t, t, nrm);
+    }
+  }
+  double v[1] = {nrm};
+  block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
+  if (last_block(st)) gmres_init_last(st, partials, m, max_it, rtol, force);
+}
+
+// adjoint: b_i = h b_i lambda (the right-hand side of A^T mu = h (b (x) lambda))
+template <int S>
+__global__ void __launch_bounds__(BS)
+k_rhs_adjoint(int n, KronCoef hb, const double* __restrict__ lam, double* __restrict__ b,
+              double* __restrict__ V0, double* __restrict__ x, GmresState* st, double* __restrict__ partials,
+              int m, int max_it, double rtol, int force) {
+  double nrm = 0.0;
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    double l = lam[r];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double t = hb.a[i] * l;
+      b[int64_t(i) * n + r] = t;
+      V0[int64_t(i) * n + r] = t;
+      x[int64_t(i) * n + r] = 0.0;
+      nrm = fma(t, t, nrm);
+    }
+  }
+  double v[1] = {nrm};
+  block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
+  if (last_block(st)) gmres_init_last(st, partials, m, max_it, rtol, force);
+}
+
+// u += sum_i (h b_i) k_i   (Section 2)
+template <int S>
+__global__ void __launch_bounds__(BS)
+k_stage_update(int n, KronCoef hb, const double* __restrict__ k, double* __restrict__ u) {
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    double s = u[r];
+#pragma unroll
+    for (int i = 0; i < S; ++i) s = fma(hb.a[i], k[int64_t(i) * n + r], s);
+    u[r] = s;
+  }
+}
+
+__global__ void k_record(const GmresState* st, StepRecord* rec, int* counter, int cap) {
+  if (threadIdx.x || blockIdx.x) return;
+  int q = *counter;
+  if (q < cap) {
+    rec[q].it = st->it;
+    rec[q].restarts = st->restarts;
+    rec[q].status = st->status;
+    rec[q].resid = st->resid;
+  }
+  *counter = q + 1;
+}
+
+// y = M x
+__global__ void __launch_bounds__(BS)
+k_spmv64(int n, SellView<double> A, const double* __restrict__ x, double* __restrict__ y) {
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = A.sptr[sl];
+    int wdt = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
+    double t = 0.0;
+    for (int k = 0; k < wdt; ++k) {
+      int64_t idx = base + (int64_t(k) << 5) + lane;
+      t = fma(A.val[idx], x[A.col[idx]], t);
+    }
+    y[r] = t;
+  }
+}
+
+// lambda_n = lambda_{n+1} - F^T sum_i mu_i   (F symmetric)
+template <int S>
+__global__ void __launch_bounds__(BS)
+k_adj_lambda(int n, SellView<double> Fv, const double* __restrict__ mu, const double* __restrict__ lin,
+             double* __restrict__ lout) {
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = Fv.sptr[sl];
+    int wdt = static_cast<int>((Fv.sptr[sl + 1] - base) >> 5);
+    double t = 0.0;
+    for (int k = 0; k < wdt; ++k) {
+      int64_t idx = base + (int64_t(k) << 5) + lane;
+      int c = Fv.col[idx];
+      double ms = 0.0;
+#pragma unroll
+      for (int i = 0; i < S; ++i) ms += mu[int64_t(i) * n + c];
+      t = fma(Fv.val[idx], ms, t);
+    }
+    lout[r] = lin[r] - t;
+  }
+}
+
+// dL/dkappa_e += -sum_i mu_i[e]^T K_e U_i[e],  U_i = u + sum_j (h a_ij) k_j
+template <int S>
+__global__ void __launch_bounds__(BS)
+k_adj_grad(int n_tri, const int* __restrict__ tri, const int* __restrict__ dof, const double* __restrict__ Ke,
+           KronCoef K, int n, const double* __restrict__ u, const double* __restrict__ kst,
+           const double* __restrict__ mu, double* __restrict__ grad) {
+  for (int e = blockIdx.x * BS + threadIdx.x; e < n_tri; e += gridDim.x * BS) {
+    int d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = dof[tri[3 * e + a]];
+    double ke[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ke[q] = Ke[int64_t(e) * 9 + q];
+    double kv[S][3];
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) kv[j][a] = d[a] >= 0 ? kst[int64_t(j) * n + d[a]] : 0.0;
+    double ua[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ua[a] = d[a] >= 0 ? u[d[a]] : 0.0;
+    double gsum = 0.0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double U[3], m3[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double t = ua[a];
+#pragma unroll
+        for (int j = 0; j < S; ++j) t = fma(K.a[i * MAX_S + j], kv[j][a], t);
+        U[a] = t;
+        m3[a] = d[a] >= 0 ? mu[int64_t(i) * n + d[a]] : 0.0;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) gsum = fma(m3[a] * ke[a * 3 + bb], U[bb], gsum);
+    }
+    grad[e] -= gsum;
+  }
+}
+
+// F values = sum over contributions kappa_e K_e[a][b] (deterministic gather)
+__global__ void __launch_bounds__(BS)
+k_assemble_kappa(int64_t nnz, const int* __restrict__ ptr, const int* __restrict__ src,
+                 const double* __restrict__ Ke, const double* __restrict__ kappa, double* __restrict__ Fval) {
+  for (int64_t q = blockIdx.x * int64_t(BS) + threadIdx.x; q < nnz; q += int64_t(gridDim.x) * BS) {
+    double s = 0.0;
+    for (int t = ptr[q]; t < ptr[q + 1]; ++t) {
+      int c = src[t];
+      s += kappa[c / 9] * Ke[c];
+    }
+    Fval[q] = s;
+  }
+}
+
+__global__ void k_convert(const void* in, int ip, void* out, int op, int64_t n) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  double v = ip == 64 ? static_cast<const double*>(in)[i] : static_cast<double>(static_cast<const float*>(in)[i]);
+  if (op == 64) static_cast<double*>(out)[i] = v;
+  else static_cast<float*>(out)[i] = static_cast<float>(v);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+#define IRK_DISPATCH_S(S_, ...)                              \
+  switch (S_) {                                              \
+    case 1: { constexpr int S = 1; __VA_ARGS__; } break;     \
+    case 2: { constexpr int S = 2; __VA_ARGS__; } break;     \
+    case 3: { constexpr int S = 3; __VA_ARGS__; } break;     \
+    case 4: { constexpr int S = 4; __VA_ARGS__; } break;     \
+    case 5: { constexpr int S = 5; __VA_ARGS__; } break;     \
+    case 6: { constexpr int S = 6; __VA_ARGS__; } break;     \
+    case 7: { constexpr int S = 7; __VA_ARGS__; } break;     \
+    case 8: { constexpr int S = 8; __VA_ARGS__; } break;     \
+    default: fail(IRK_ERR_INVALID, "s must be 1..8");        \
+  }
+
+static unsigned row_grid(const Ctx& c) { return static_cast<unsigned>(c.gs_grid); }
+
+// One FGMRES iteration after the preconditioner: w = A z_j into V_{j+1},
+// Gram-Schmidt, Givens, and at a cycle end x += Z y and the true residual.
+int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
+  const KronCoef& K = transpose ? c.KT : c.K;
+  int n = c.n;
+  int64_t N = c.N;
+  int launches = 0;
+  unsigned G = row_grid(c);
+  const int* jp = &c.st->j;
+  bool z32 = c.amg.amg_prec != 64;
+  IRK_DISPATCH_S(c.s, {
+    if (z32)
+      k_kron<S, float, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+                                            JPtr<const float>{static_cast<const float*>(c.Z), jp, N, 0, 0},
+                                            JPtr<double>{c.V, jp, N, 1, 0}, K, nullptr, c.st, c.partials);
+    else
+      k_kron<S, double, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+                                             JPtr<const double>{static_cast<const double*>(c.Z), jp, N, 0, 0},
+                                             JPtr<double>{c.V, jp, N, 1, 0}, K, nullptr, c.st, c.partials);
+  });
+  ++launches;
+  k_gs_dots<0><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
+  k_gs_axpy<0><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
+  k_gs_dots<1><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
+  k_gs_axpy<1><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
+  launches += 4;
+  if (z32)
+    k_xupdate<float><<<G, BS, 0, st>>>(c.st, static_cast<const float*>(c.Z), N, c.x, N);
+  else
+    k_xupdate<double><<<G, BS, 0, st>>>(c.st, static_cast<const double*>(c.Z), N, c.x, N);
+  ++launches;
+  IRK_DISPATCH_S(c.s, {
+    k_kron<S, double, 1><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64, JPtr<const double>{c.x, nullptr, 0, 0, 0},
+                                           JPtr<double>{c.V, nullptr, 0, 0, 0}, K, c.bv, c.st, c.partials);
+  });
+  ++launches;
+  CK_LAUNCH();
+  return launches;
+}
+
+void set_loop_condition_launch(Ctx& c, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_loop_ctrl<<<1, 32, 0, st>>>(c.st, h);
+  CK_LAUNCH();
+}
+
+void rhs_forward_launch(Ctx& c, const double* u, cudaStream_t st) {
+  IRK_DISPATCH_S(c.s, {
+    k_rhs_forward<S><<<row_grid(c), BS, 0, st>>>(c.n, view<double>(c.Fs), u, c.g, c.bv, c.V, c.x, c.st, c.partials,
+                                                 c.m, c.max_it, c.rtol, c.reorth);
+  });
+  CK_LAUNCH();
+}
+
+void rhs_adjoint_launch(Ctx& c, const double* lam, cudaStream_t st) {
+  KronCoef hb;
+  for (int i = 0; i < MAX_S * MAX_S; ++i) hb.a[i] = 0.0;
+  for (int i = 0; i < c.s; ++i) hb.a[i] = c.h * c.b[i];
+  IRK_DISPATCH_S(c.s, {
+    k_rhs_adjoint<S><<<row_grid(c), BS, 0, st>>>(c.n, hb, lam, c.bv, c.V, c.x, c.st, c.partials, c.m, c.max_it,
+                                                 c.rtol, c.reorth);
+  });
+  CK_LAUNCH();
+}
+
+void stage_update_launch(Ctx& c, double* u, cudaStream_t st) {
+  KronCoef hb;
+  for (int i = 0; i < MAX_S * MAX_S; ++i) hb.a[i] = 0.0;
+  for (int i = 0; i < c.s; ++i) hb.a[i] = c.h * c.b[i];
+  IRK_DISPATCH_S(c.s, { k_stage_update<S><<<row_grid(c), BS, 0, st>>>(c.n, hb, c.x, u); });
+  CK_LAUNCH();
+}
+
+void record_launch(Ctx& c, cudaStream_t st) {
+  k_record<<<1, 32, 0, st>>>(c.st, c.rec, c.step_counter, c.rec_cap);
+  CK_LAUNCH();
+}
+
+void kron_apply_plain(Ctx& c, const double* z, double* w, bool transpose, cudaStream_t st) {
+  const KronCoef& K = transpose ? c.KT : c.K;
+  IRK_DISPATCH_S(c.s, {
+    k_kron<S, double, 0><<<row_grid(c), BS, 0, st>>>(c.n, view<double>(c.Ms), c.Fs.v64,
+                                                     JPtr<const double>{z, nullptr, 0, 0, 0},
+                                                     JPtr<double>{w, nullptr, 0, 0, 0}, K, nullptr, nullptr, nullptr);
+  });
+  CK_LAUNCH();
+}
+
+void mass_apply_launch(Ctx& c, const double* x, double* y, cudaStream_t st) {
+  k_spmv64<<<row_grid(c), BS, 0, st>>>(c.n, view<double>(c.Ms), x, y);
+  CK_LAUNCH();
+}
+
+void adjoint_lambda_launch(Ctx& c, const double* lam_in, double* lam_out, cudaStream_t st) {
+  IRK_DISPATCH_S(c.s, { k_adj_lambda<S><<<row_grid(c), BS, 0, st>>>(c.n, view<double>(c.Fs), c.x, lam_in, lam_out); });
+  CK_LAUNCH();
+}
+
+void adjoint_grad_launch(Ctx& c, const double* u_n, const double* k_n, double* grad, cudaStream_t st) {
+  IRK_DISPATCH_S(c.s, {
+    k_adj_grad<S><<<row_grid(c), BS, 0, st>>>(c.n_tri, c.tri, c.dof, c.Ke, c.K, c.n, u_n, k_n, c.x, grad);
+  });
+  CK_LAUNCH();
+}
+
+void assemble_kappa_launch(Ctx& c, const double* kappa, double* Fval, cudaStream_t st) {
+  k_assemble_kappa<<<row_grid(c), BS, 0, st>>>(c.Fc.nnz, c.asm_ptr, c.asm_src, c.Ke, kappa, Fval);
+  CK_LAUNCH();
+}
+
+void convert_launch(const void* in, int in_prec, void* out, int out_prec, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_convert<<<nblk(n), 256, 0, st>>>(in, in_prec, out, out_prec, n);
+  CK_LAUNCH();
+}
+
+}  // namespace irk

@@ -1,0 +1,394 @@
+// One AMG V-cycle per diagonal-block subsolve, and the block substitutions of
+// Section 4.2 that apply P = I_s (x) M + h A~ (x) F.
+//
+// V(nu1, nu2) cycle on a hierarchy built by amg_setup.cu; each smoothing sweep
+// is a Chebyshev polynomial on the l1-scaled operator D_l1^{-1} A (or one
+// l1-Jacobi step).  Kernels are one thread per row over SELL-32 matrices (each
+// warp reads one slice: coalesced column/value loads), values in the V-cycle
+// precision T (FP32 or FP64; BF16 finest-level values are widened to FP32).
+// The first pre-smoothing step from a zero guess needs no matrix product; its
+// iterate is recomputed from b where a neighbour needs it.
+#include "irk_internal.cuh"
+
+#include <cmath>
+
+namespace irk {
+
+template <typename T> __device__ __forceinline__ T widen(T v) { return v; }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+SmoothCoef smooth_coefficients(const AmgParams& p) {
+  SmoothCoef c;
+  if (p.smoother == IRK_SMOOTH_L1JACOBI) {
+    c.steps = 1;
+    c.alpha[0] = 0.0;
+    c.beta[0] = 1.0;
+    return c;
+  }
+  int k = p.cheb_degree < 1 ? 1 : (p.cheb_degree > 16 ? 16 : p.cheb_degree);
+  double lo = p.cheb_lo;
+  double theta = 0.5 * (1.0 + lo), delta = 0.5 * (1.0 - lo);
+  double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  c.steps = k;
+  c.alpha[0] = 0.0;
+  c.beta[0] = 1.0 / theta;
+  for (int i = 1; i < k; ++i) {
+    double rn = 1.0 / (2.0 * sigma - rho);
+    c.alpha[i] = rn * rho;
+    c.beta[i] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  return c;
+}
+
+// x^(0) implicit: x1 = beta0 * dinv * b
+enum { XM_EXPLICIT = 0, XM_IMPLICIT = 1, XM_ZERO = 2 };
+
+// One smoothing step: d = alpha d_prev + beta D^{-1}(b - A x); x_out = x + d.
+// XM_IMPLICIT: x and d_prev are the implicit first step; XM_ZERO: x = 0, no product.
+template <typename V, typename T, int XM>
+__global__ void __launch_bounds__(256)
+k_smooth(SellView<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ xin,
+         const T* din, T* __restrict__ xout, T* dout, T alpha, T beta, T beta0,
+         JPtr<T> out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.n) return;
+  T ax = T(0);
+  if (XM != XM_ZERO) {
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = A.sptr[sl];
+    int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
+    for (int k = 0; k < w; ++k) {
+      int64_t idx = base + (int64_t(k) << 5) + lane;
+      int c = A.col[idx];
+      T v = widen(A.val[idx]);
+      T xc = (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : xin[c];
+      ax = fma(v, xc, ax);
+    }
+  }
+  T dr = dinv[r], br = b[r];
+  T xr, dprev;
+  if (XM == XM_EXPLICIT) {
+    xr = xin[r];
+    dprev = din ? din[r] : T(0);
+  } else if (XM == XM_IMPLICIT) {
+    xr = beta0 * dr * br;
+    dprev = xr;
+  } else {
+    xr = T(0);
+    dprev = T(0);
+  }
+  T res = dr * (br - ax);
+  T d = alpha * dprev + beta * res;
+  T xn = xr + d;
+  if (out.base) out.get()[r] = xn;
+  else xout[r] = xn;
+  if (dout) dout[r] = d;
+}
+
+// r = b - A x  (x explicit or the implicit first step)
+template <typename V, typename T, int XM>
+__global__ void __launch_bounds__(256)
+k_resid(SellView<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
+        T beta0, T* __restrict__ r_out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.n) return;
+  int sl = r >> 5, lane = r & 31;
+  int64_t base = A.sptr[sl];
+  int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
+  T ax = T(0);
+  for (int k = 0; k < w; ++k) {
+    int64_t idx = base + (int64_t(k) << 5) + lane;
+    int c = A.col[idx];
+    T xc = (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : x[c];
+    ax = fma(widen(A.val[idx]), xc, ax);
+  }
+  r_out[r] = b[r] - ax;
+}
+
+// y = R x (restriction)
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.n) return;
+  int sl = r >> 5, lane = r & 31;
+  int64_t base = A.sptr[sl];
+  int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
+  T s = T(0);
+  for (int k = 0; k < w; ++k) {
+    int64_t idx = base + (int64_t(k) << 5) + lane;
+    s = fma(A.val[idx], x[A.col[idx]], s);
+  }
+  y[r] = s;
+}
+
+// x += P e (prolongation and correction), x_implicit: x starts as beta0 dinv b
+template <typename T, bool IMPLICIT>
+__global__ void __launch_bounds__(256)
+k_prolong(SellView<T> P, const T* __restrict__ e, T* x, const T* __restrict__ dinv,
+          const T* __restrict__ b, T beta0) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.n) return;
+  int sl = r >> 5, lane = r & 31;
+  int64_t base = P.sptr[sl];
+  int w = static_cast<int>((P.sptr[sl + 1] - base) >> 5);
+  T s = IMPLICIT ? beta0 * dinv[r] * b[r] : x[r];
+  for (int k = 0; k < w; ++k) {
+    int64_t idx = base + (int64_t(k) << 5) + lane;
+    s = fma(P.val[idx], e[P.col[idx]], s);
+  }
+  x[r] = s;
+}
+
+// coarsest level: x = A^{-1} b with the stored dense inverse; one warp per row
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, JPtr<T> out) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const T* row = Ainv + size_t(warp) * n;
+  T s = T(0);
+  for (int c = lane; c < n; c += 32) s = fma(row[c], b[c], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    if (out.base) out.get()[warp] = s;
+    else x[warp] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) out.get()[r] = src[r];
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle driver (kernel sequence; captured into CUDA graphs by the caller)
+// ---------------------------------------------------------------------------
+template <typename T, typename V0>
+struct VCycle {
+  const Hier& H;
+  const AmgParams& p;
+  const SmoothCoef& sc;
+  cudaStream_t st;
+  int launches = 0;
+
+  template <typename V, int XM>
+  void smooth(const Level& L, const T* xin, const T* din, T* xout, T* dout, int step, JPtr<T> out) {
+    k_smooth<V, T, XM><<<nblk(L.n), 256, 0, st>>>(view<V>(L.As), static_cast<const T*>(L.dinv),
+                                                  static_cast<const T*>(L.b), xin, din, xout, dout,
+                                                  T(sc.alpha[step]), T(sc.beta[step]), T(sc.beta[0]), out);
+    ++launches;
+  }
+
+  // returns the buffer holding the level's result (or nullptr if written to out)
+  template <typename V>
+  T* level(int l, JPtr<T> out) {
+    const Level& L = H.lv[l];
+    T* b = static_cast<T*>(L.b);
+    T* xb = static_cast<T*>(L.x);
+    T* yb = static_cast<T*>(L.y);
+    T* db = static_cast<T*>(L.d);
+    T* rb = static_cast<T*>(L.r);
+    JPtr<T> none = jptr<T>(nullptr);
+    int last = static_cast<int>(H.lv.size()) - 1;
+    if (l == last) {
+      int nl = L.n;
+      unsigned blocks = nblk(int64_t(nl) * 32);
+      k_dense_mv<T><<<blocks, 256, 0, st>>>(nl, static_cast<const T*>(H.cinv), b, xb, out);
+      ++launches;
+      return out.base ? nullptr : xb;
+    }
+    const int steps = sc.steps;
+    // ---- pre-smoothing from zero
+    bool implicit = false;   // x = beta0 dinv b, d = x, not materialised
+    T* cur = xb;
+    T* oth = yb;
+    for (int sw = 0; sw < p.nu_pre; ++sw) {
+      for (int k = 0; k < steps; ++k) {
+        if (sw == 0 && k == 0) {
+          implicit = true;
+          continue;
+        }
+        if (implicit) {
+          smooth<V, XM_IMPLICIT>(L, nullptr, nullptr, cur, db, k, none);
+          implicit = false;
+        } else {
+          smooth<V, XM_EXPLICIT>(L, cur, k == 0 ? nullptr : db, oth, db, k, none);
+          T* t = cur;
+          cur = oth;
+          oth = t;
+        }
+      }
+    }
+    // ---- residual and restriction
+    const T beta0 = T(sc.beta[0]);
+    if (p.nu_pre > 0) {
+      if (implicit)
+        k_resid<V, T, XM_IMPLICIT><<<nblk(L.n), 256, 0, st>>>(view<V>(L.As), static_cast<const T*>(L.dinv), b,
+                                                              nullptr, beta0, rb);
+      else
+        k_resid<V, T, XM_EXPLICIT><<<nblk(L.n), 256, 0, st>>>(view<V>(L.As), static_cast<const T*>(L.dinv), b,
+                                                              cur, beta0, rb);
+      ++launches;
+    }
+    const Level& C = H.lv[l + 1];
+    k_spmv<T><<<nblk(C.n), 256, 0, st>>>(view<T>(L.Rs), p.nu_pre > 0 ? rb : b, static_cast<T*>(C.b));
+    ++launches;
+    T* e = level<T>(l + 1, none);
+    // ---- prolongation and correction
+    if (p.nu_pre == 0) {
+      CK(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, st));
+      k_prolong<T, false><<<nblk(L.n), 256, 0, st>>>(view<T>(L.Ps), e, cur, nullptr, nullptr, beta0);
+    } else if (implicit) {
+      k_prolong<T, true><<<nblk(L.n), 256, 0, st>>>(view<T>(L.Ps), e, cur, static_cast<const T*>(L.dinv), b,
+                                                    beta0);
+    } else {
+      k_prolong<T, false><<<nblk(L.n), 256, 0, st>>>(view<T>(L.Ps), e, cur, nullptr, nullptr, beta0);
+    }
+    ++launches;
+    // ---- post-smoothing
+    int total = p.nu_post * steps;
+    int q = 0;
+    for (int sw = 0; sw < p.nu_post; ++sw) {
+      for (int k = 0; k < steps; ++k, ++q) {
+        bool final_step = (q == total - 1);
+        JPtr<T> o = (final_step && out.base) ? out : none;
+        smooth<V, XM_EXPLICIT>(L, cur, k == 0 ? nullptr : db, oth, db, k, o);
+        T* t = cur;
+        cur = oth;
+        oth = t;
+      }
+    }
+    if (total == 0 && out.base) {
+      k_copy_out<T><<<nblk(L.n), 256, 0, st>>>(L.n, cur, out);
+      ++launches;
+    }
+    return out.base ? nullptr : cur;
+  }
+};
+
+template <typename T, typename V0>
+static int run_vcycle(const Hier& H, const AmgParams& p, const SmoothCoef& sc, JPtr<T> out,
+                      cudaStream_t st) {
+  VCycle<T, V0> vc{H, p, sc, st, 0};
+  vc.template level<V0>(0, out);
+  CK_LAUNCH();
+  return vc.launches;
+}
+
+int vcycle_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, void* out_base, const int* jp,
+                  int64_t jstride, int64_t off, cudaStream_t st) {
+  if (H.amg_prec == 64) {
+    JPtr<double> o = jptr<double>(static_cast<double*>(out_base), jp, jstride, 0, off);
+    return run_vcycle<double, double>(H, p, sc, o, st);
+  }
+  JPtr<float> o = jptr<float>(static_cast<float*>(out_base), jp, jstride, 0, off);
+  if (H.amg_prec == 16) return run_vcycle<float, __nv_bfloat16>(H, p, sc, o, st);
+  return run_vcycle<float, float>(H, p, sc, o, st);
+}
+
+// ---------------------------------------------------------------------------
+// Block substitution right-hand side (Section 4.2):
+//   rhs_j = sigma_j v_j - sum_{k in prev(j)} h A~_jk F w_k
+// one pass over F for all coupled stages; w_k are the already computed stage
+// outputs in Z[j].
+// ---------------------------------------------------------------------------
+struct Couplings {
+  int n;
+  int idx[MAX_S];
+  float c32[MAX_S];
+  double c64[MAX_S];
+};
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(256)
+k_sweep_rhs(SellView<T> F, const double* __restrict__ V, const int* __restrict__ jp, int64_t ldv,
+            int64_t voff, const double* __restrict__ sigma, const T* __restrict__ Z, int64_t ldz,
+            Couplings cp, const int* __restrict__ skip, T* __restrict__ out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = F.n;
+  if (r >= n) return;
+  if (skip && *skip) {
+    out[r] = T(0);
+    return;
+  }
+  int j = jp ? *jp : 0;
+  double sj = sigma ? sigma[j] : 1.0;
+  T v = static_cast<T>(V[int64_t(j) * ldv + voff + r] * sj);
+  if (NP == 0) {
+    out[r] = v;
+    return;
+  }
+  const T* zj = Z + int64_t(j) * ldz;
+  T acc[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) acc[q] = T(0);
+  int sl = r >> 5, lane = r & 31;
+  int64_t base = F.sptr[sl];
+  int w = static_cast<int>((F.sptr[sl + 1] - base) >> 5);
+  for (int k = 0; k < w; ++k) {
+    int64_t idx = base + (int64_t(k) << 5) + lane;
+    int c = F.col[idx];
+    T f = F.val[idx];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc[q] = fma(f, zj[int64_t(cp.idx[q]) * n + c], acc[q]);
+  }
+  T res = v;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    T cq = sizeof(T) == 8 ? static_cast<T>(cp.c64[q]) : static_cast<T>(cp.c32[q]);
+    res = fma(-cq, acc[q], res);
+  }
+  out[r] = res;
+}
+
+template <typename T>
+static void launch_sweep_rhs(int np, SellView<T> F, const double* V, const int* jp, int64_t ldv, int64_t voff,
+                             const double* sigma, const T* Z, int64_t ldz, const Couplings& cp, const int* skip,
+                             T* out, cudaStream_t st) {
+  unsigned g = nblk(F.n);
+  switch (np) {
+#define IRK_SW(NPV) \
+  case NPV: k_sweep_rhs<T, NPV><<<g, 256, 0, st>>>(F, V, jp, ldv, voff, sigma, Z, ldz, cp, skip, out); break;
+    IRK_SW(0) IRK_SW(1) IRK_SW(2) IRK_SW(3) IRK_SW(4) IRK_SW(5) IRK_SW(6) IRK_SW(7)
+#undef IRK_SW
+    default: fail(IRK_ERR_INVALID, "too many stage couplings");
+  }
+}
+
+int precond_launch(Ctx& c, const PrecondArgs& a, bool transpose, cudaStream_t st) {
+  const SweepPlan& P = transpose ? c.planT : c.plan;
+  int n = c.n;
+  int launches = 0;
+  bool f64 = c.amg.amg_prec == 64;
+  for (int pos = 0; pos < P.s; ++pos) {
+    int stage = P.order[pos];
+    const Hier& H = c.hiers[P.hier[pos]];
+    Couplings cp;
+    cp.n = P.nprev[pos];
+    for (int q = 0; q < MAX_S; ++q) {
+      cp.idx[q] = q < cp.n ? P.prev[pos][q] : 0;
+      cp.c64[q] = q < cp.n ? P.coef[pos][q] : 0.0;
+      cp.c32[q] = static_cast<float>(cp.c64[q]);
+    }
+    if (f64) {
+      launch_sweep_rhs<double>(cp.n, view<double>(c.Fs), a.V, a.jp, a.ldv, int64_t(stage) * n, a.sigma,
+                               static_cast<const double*>(a.Z), a.ldz, cp, a.skip,
+                               static_cast<double*>(H.lv[0].b), st);
+    } else {
+      launch_sweep_rhs<float>(cp.n, view<float>(c.Fs), a.V, a.jp, a.ldv, int64_t(stage) * n, a.sigma,
+                              static_cast<const float*>(a.Z), a.ldz, cp, a.skip, static_cast<float*>(H.lv[0].b),
+                              st);
+    }
+    CK_LAUNCH();
+    ++launches;
+    launches += vcycle_launch(H, c.amg, c.sc, a.Z, a.jp, a.ldz, int64_t(stage) * n, st);
+  }
+  return launches;
+}
+
+}  // namespace irk

@@ -1,0 +1,147 @@
+"""CPU tests of libirk without a GPU: the library loads, exports every entry
+point declared in include/irk.h, and its host-side tables and P1 assembly
+match the oracle (no device work is done here)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import butcher as obt
+from oracle import fem as ofem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2010_11377_gb300.build import build
+    build()
+    from paper_2010_11377_gb300._abi import lib
+    return lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "irk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(irk_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 20
+    for nm in names:
+        assert hasattr(L, nm), nm
+    from paper_2010_11377_gb300._abi import SIGNATURES
+    assert sorted(n for n, _, _ in SIGNATURES) == names
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    import paper_2010_11377_gb300._abi as abi
+    monkeypatch.setattr(abi, "_lib", None)
+    monkeypatch.setattr(abi, "LIB", "/nonexistent/libirk.so")
+    with pytest.raises(RuntimeError):
+        abi.lib()
+
+
+@pytest.mark.parametrize("s", range(1, 9))
+def test_radau_table_matches_oracle(L, s):
+    from paper_2010_11377_gb300 import binding as B
+    A, b, c = B.irk_butcher_table("radau_iia", s)
+    if s <= 7:
+        OA, Ob, Oc = obt.radau_iia(s)
+        assert np.max(np.abs(A - OA)) < 1e-14 and np.max(np.abs(b - Ob)) < 1e-14
+        assert np.max(np.abs(c - Oc)) < 1e-15
+    for q in range(1, 2 * s):
+        assert abs(b @ c ** (q - 1) - 1.0 / q) < 1e-13
+
+
+@pytest.mark.parametrize("s", range(2, 6))
+def test_lobatto_table_matches_oracle(L, s):
+    from paper_2010_11377_gb300 import binding as B
+    A, b, c = B.irk_butcher_table("lobatto_iiic", s)
+    OA, Ob, Oc = obt.lobatto_iiic(s)
+    assert np.max(np.abs(A - OA)) < 1e-14 and np.max(np.abs(b - Ob)) < 1e-14
+
+
+def test_ldu_and_atilde_match_oracle(L):
+    from paper_2010_11377_gb300 import binding as B
+    for s in range(2, 8):
+        A, _, _ = obt.radau_iia(s)
+        Lm, D, U = B.irk_ldu(A)
+        OL, OD, OU = obt.ldu(A)
+        assert np.allclose(Lm, OL, atol=1e-13) and np.allclose(D, np.diag(OD), atol=1e-15)
+        assert np.allclose(U, OU, atol=1e-13)
+        for kind in ("J", "GSL", "DU", "LD"):
+            At, kap = B.irk_atilde(kind, A)
+            assert np.allclose(At, obt.atilde(A, kind), atol=1e-14)
+            ref = obt.kappa2(np.linalg.solve(obt.atilde(A, kind), A))
+            assert abs(kap - ref) < 1e-9 * ref
+    from paper_2010_11377_gb300._abi import IrkError
+    with pytest.raises(IrkError):
+        B.irk_ldu(np.array([[0.0, 1.0], [1.0, 0.0]]))
+
+
+def test_gsl_opt_matches_oracle_optimum(L):
+    """Eq. GSLopt solved by the library's own Nelder-Mead: the optimum is
+    lower triangular with diag(A), and its kappa is within 2% of the oracle's."""
+    from paper_2010_11377_gb300 import binding as B
+    for s in range(2, 8):
+        A, _, _ = obt.radau_iia(s)
+        At, kap = B.irk_atilde("GSL_OPT", A)
+        assert np.allclose(np.diag(At), np.diag(A)) and np.allclose(np.triu(At, 1), 0)
+        ko = obt.kappa2(np.linalg.solve(obt.gsl_optimized(A), A))
+        assert kap <= obt.kappa2(np.linalg.solve(np.tril(A), A)) + 1e-12
+        assert kap <= 1.02 * ko, (s, kap, ko)
+
+
+def _csr(rp, col, val, n):
+    import scipy.sparse as sp
+    return sp.csr_matrix((val, col, rp), shape=(n, n))
+
+
+@pytest.mark.parametrize("N", [5, 16])
+def test_fem_heat_matches_oracle(L, N):
+    from paper_2010_11377_gb300 import binding as B
+    mesh = synth.structured_mesh(N)
+    kap = np.exp(synth.grf_log_kappa(mesh, seed=2))
+    rp, col, vM, vF, g = B.irk_fem_assemble(mesh.xy, mesh.tri, mesh.dof, mesh.n, kappa=kap)
+    prob = ofem.heat_problem(mesh, kappa=kap)
+    assert abs(_csr(rp, col, vM, mesh.n) - prob.M).max() < 1e-15
+    assert abs(_csr(rp, col, vF, mesh.n) - prob.F).max() < 1e-12 * abs(prob.F).max()
+    assert np.all(g == 0)
+
+
+def test_fem_double_glazing_matches_oracle(L):
+    """Different exact quadrature rules on both sides (Dunavant degree 4 here,
+    collapsed Gauss in the oracle) give the same convection matrix."""
+    from paper_2010_11377_gb300 import problems
+    p = problems.double_glazing(12, eps=0.005)
+    mesh = p["mesh"]
+    prob = ofem.double_glazing_problem(mesh, 0.005, synth.double_glazing_wind, synth.double_glazing_boundary(mesh))
+    F = _csr(p["rowptr"], p["col"], p["valF"], mesh.n)
+    assert abs(F - prob.F).max() < 1e-13 * abs(prob.F).max()
+    assert np.max(np.abs(p["g"] - prob.g)) < 1e-13
+    assert abs(_csr(p["rowptr"], p["col"], p["valM"], mesh.n) - prob.M).max() < 1e-16
+
+
+def test_fem_quad_rule_exact_degree4(L):
+    """The convection rule integrates every monomial of degree <= 4 exactly:
+    with the wind w = (x^a y^b, 0) on one reference-like triangle, sum of the
+    C row entries against linear data reproduces int x^a y^b dphi/dx."""
+    from paper_2010_11377_gb300 import binding as B
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [2.0, 2.0]])
+    tri = np.array([[0, 1, 2]], dtype=np.int32)
+    dof = np.array([0, 1, 2, -1], dtype=np.int32)
+    from math import factorial
+    for a in range(5):
+        for bexp in range(5 - a):
+            xq = B.irk_fem_quad_points(xy, tri)
+            wind = np.zeros_like(xq)
+            wind[..., 0] = xq[..., 0] ** a * xq[..., 1] ** bexp
+            rp, col, vM, vF, g = B.irk_fem_assemble(xy, tri, dof, 3, kappa=np.zeros(1), wind=wind)
+            C = _csr(rp, col, vF, 3).toarray()
+            # sum_k C[k, l] = int w . grad phi_l ; for l = 1 (phi = x): int x^a y^b
+            exact = factorial(a) * factorial(bexp) / factorial(a + bexp + 2)
+            assert abs(C[:, 1].sum() - exact) < 1e-14, (a, bexp)

@@ -1,0 +1,327 @@
+"""GPU parity: libirk (through the C ABI) against the FP64 oracle on the same
+seeded inputs.  Sizes span several 32-row slices with a ragged tail."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import amg as oamg
+from oracle import butcher as obt
+from oracle import fem as ofem
+from oracle import irk as oirk
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_11377_gb300.build import build
+    build()
+
+
+def B():
+    from paper_2010_11377_gb300 import binding
+    return binding
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def oracle_ctx(prob, A, kind, h, amg_prec="f64", mesh=None, b=None, **opt):
+    """GPU context on the oracle's own matrices, Butcher table and A~ (so both
+    sides start from bit-identical data)."""
+    bnd = B()
+    At = obt.atilde(A, kind)
+    M = prob.M.tocsr()
+    M.sort_indices()
+    F = M.copy()
+    coo = M.tocoo()
+    # F on the pattern of M (scipy drops exact zeros from sums such as eps K + C)
+    F.data = np.asarray(prob.F.tocsr()[coo.row, coo.col]).ravel()
+    At_c = np.ascontiguousarray(At, dtype=np.float64)
+    o = bnd.irk_default_options(kind="CUSTOM", amg_prec=amg_prec, **opt)
+    o.Atilde = At_c.ctypes.data_as(bnd._abi.c_double_p)
+    bw = A[-1].copy() if b is None else b
+    ctx = bnd.irk_setup(M.indptr.astype(np.int64), M.indices, M.data, F.data,
+                        (A, bw, np.zeros(A.shape[0])), h, options=o, g=prob.g, mesh=mesh)
+    ctx._keep = At_c
+    return ctx, At
+
+
+def heat(N, kappa=None):
+    mesh = synth.structured_mesh(N)
+    return mesh, ofem.heat_problem(mesh, kappa=kappa)
+
+
+def dg(N, eps=1 / 200):
+    mesh = synth.structured_mesh(N, "box")
+    return mesh, ofem.double_glazing_problem(mesh, eps, synth.double_glazing_wind,
+                                             synth.double_glazing_boundary(mesh))
+
+
+AMG_OPTS = dict(theta=0.08, coarse_max=256, smoother="chebyshev", cheb_degree=3, cheb_lo=0.1)
+
+
+def oracle_amg_opts():
+    return dict(theta=0.08, coarse_max=256, smoother="chebyshev", cheb_degree=3, cheb_lo=0.1)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("s", [1, 3, 7])
+def test_operator_parity(s):
+    mesh, prob = heat(41)
+    A, _, _ = obt.radau_iia(s)
+    h = 1 / 64
+    ctx, _ = oracle_ctx(prob, A, "LD" if s > 1 else "J", h)
+    z = synth.random_stage_block(prob.n, s, 11)
+    for tr in (False, True):
+        w = torch.empty(s * prob.n, dtype=torch.float64, device="cuda")
+        B().irk_apply_operator(ctx, dev(z.ravel()), w, transpose=tr)
+        Am = A.T if tr else A
+        ref = oirk.apply_operator(prob.M, prob.F, Am, h, z)
+        err = np.max(np.abs(host(w).reshape(s, -1) - ref)) / np.max(np.abs(ref))
+        assert err < 1e-14, err
+    x = synth.random_stage_block(prob.n, 1, 3)[0]
+    y = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    B().irk_apply_mass(ctx, dev(x), y)
+    assert np.max(np.abs(host(y) - prob.M @ x)) < 1e-15 * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("which", ["heat", "dg"])
+def test_aggregates_and_galerkin_parity(which):
+    mesh, prob = heat(57) if which == "heat" else dg(57)
+    A, _, _ = obt.radau_iia(3)
+    h = 1 / 64 if which == "heat" else 0.01
+    ctx, At = oracle_ctx(prob, A, "LD", h, **AMG_OPTS)
+    for stage in range(3):
+        Bk = (prob.M + (h * At[stage, stage]) * prob.F).tocsr()
+        H = oamg.Hierarchy(Bk, **oracle_amg_opts())
+        rows, nnz = B().irk_amg_info(ctx, stage)
+        assert rows[0] == prob.n
+        # level 0: bit-identical block, identical aggregates
+        rp, col, val = B().irk_amg_level_matrix(ctx, stage, 0)
+        L0 = sp.csr_matrix((val, col, rp), shape=(prob.n, prob.n))
+        assert abs(L0 - H.levels[0].A).max() == 0.0
+        agg = B().irk_amg_aggregates(ctx, stage, 0)
+        assert np.array_equal(agg, H.levels[0].agg)
+        assert rows == H.sizes()
+        # Galerkin coarse matrices agree to rounding
+        for l in range(1, len(rows)):
+            rp, col, val = B().irk_amg_level_matrix(ctx, stage, l)
+            Lg = sp.csr_matrix((val, col, rp), shape=(rows[l], rows[l]))
+            Lo = H.levels[l].A
+            assert abs(Lg - Lo).max() <= 1e-13 * abs(Lo).max()
+            if l + 1 < len(rows):
+                assert np.array_equal(B().irk_amg_aggregates(ctx, stage, l), H.levels[l].agg)
+
+
+def bf16_round(x):
+    """Round FP64 values to the nearest BF16 value (8 significant bits,
+    ties to even), as __double2bfloat16 does."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0), e - 8)
+
+
+def test_bf16_rounding_definition():
+    assert bf16_round(1.0 + 2.0 ** -8) == 1.0                      # tie -> even
+    assert bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6      # tie -> even
+    assert bf16_round(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7          # representable
+    assert bf16_round(-3.0) == -3.0 and bf16_round(0.0) == 0.0
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 2e-5)])
+def test_vcycle_parity(prec, tol):
+    """One V-cycle against the oracle's.  BF16 stores the finest-level values
+    in BF16 (smoother and residual products); the oracle then runs the same
+    V-cycle with those rounded finest values and everything else unchanged."""
+    mesh, prob = heat(45)
+    A, _, _ = obt.radau_iia(2)
+    h = 0.05
+    ctx, At = oracle_ctx(prob, A, "LD", h, amg_prec=prec, **AMG_OPTS)
+    rhs = synth.random_stage_block(prob.n, 1, 5)[0]
+    for stage in range(2):
+        Bk = (prob.M + (h * At[stage, stage]) * prob.F).tocsr()
+        H = oamg.Hierarchy(Bk, **oracle_amg_opts())
+        exact_ref = H.vcycle(rhs)
+        if prec == "bf16":
+            A0 = H.levels[0].A.copy()
+            A0.data = bf16_round(A0.data)
+            H.levels[0].A = A0
+        ref = H.vcycle(rhs)
+        x = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        B().irk_vcycle(ctx, stage, dev(rhs), x)
+        err = np.linalg.norm(host(x) - ref) / np.linalg.norm(ref)
+        assert err < tol, (prec, stage, err)
+        if prec == "bf16":   # the rounded operator stays close to the FP64 one
+            assert np.linalg.norm(host(x) - exact_ref) < 0.1 * np.linalg.norm(exact_ref)
+
+
+@pytest.mark.parametrize("kind", ["J", "GSL", "GSL_OPT", "DU", "LD"])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
+def test_precond_parity(kind, prec, tol):
+    mesh, prob = heat(38)
+    A, _, _ = obt.radau_iia(4)
+    h = 1 / 64
+    ctx, At = oracle_ctx(prob, A, kind, h, amg_prec=prec, **AMG_OPTS)
+    v = synth.random_stage_block(prob.n, 4, 9)
+    for tr in (False, True):
+        pc = oirk.BlockPreconditioner(prob.M, prob.F, A, h, kind, "amg", Atilde=At, amg_opts=oracle_amg_opts(),
+                                      transpose=tr)
+        ref = pc.apply(v)
+        z = torch.empty(4 * prob.n, dtype=torch.float64, device="cuda")
+        B().irk_apply_precond(ctx, dev(v.ravel()), z, transpose=tr)
+        err = np.linalg.norm(host(z).reshape(4, -1) - ref) / np.linalg.norm(ref)
+        assert err < tol, (kind, prec, tr, err)
+
+
+def _its_close(a, b):
+    return abs(a - b) <= max(1, int(np.ceil(0.1 * b)))
+
+
+@pytest.mark.parametrize("kind", ["J", "GSL", "DU", "LD"])
+def test_heat_c1_run(kind):
+    """32x32 heat, Radau IIA s=2, h_t=0.05, 20 steps: every step within 1e-8
+    of the oracle's exact stage solve; FGMRES iteration counts within 10% of
+    the oracle's FGMRES with the same AMG reading."""
+    mesh, prob = heat(32)
+    A, b, _ = obt.radau_iia(2)
+    h, nsteps = 0.05, 20
+    ctx, At = oracle_ctx(prob, A, kind, h, amg_prec="f32", b=b, **AMG_OPTS)
+    u0 = synth.heat_u0(mesh)
+    direct = oirk.IRKSolver(prob, A, b, h, kind=None)
+    refs, _ = direct.run(u0, nsteps, direct=True)
+    amg_sol = oirk.IRKSolver(prob, A, b, h, kind=kind, subsolve="amg", amg_opts=oracle_amg_opts(), Atilde=At)
+    u = dev(u0)
+    for t in range(nsteps):
+        out = torch.empty_like(u)
+        st = B().irk_step(ctx, u, out)
+        got = host(out)
+        err = np.linalg.norm(got - refs[t + 1]) / np.linalg.norm(refs[t + 1])
+        assert err < 1e-8, (t, err)
+        if t < 3:
+            oit = amg_sol.step(refs[t]).iterations
+            assert _its_close(st["iterations"], oit), (t, st["iterations"], oit)
+        assert st["resid"] <= 1e-10
+        u = out
+    # the same through irk_run with checkpoints
+    uN = torch.empty_like(u)
+    ck = torch.empty((nsteps + 4) // 5, prob.n, dtype=torch.float64, device="cuda")
+    st = B().irk_run(ctx, dev(u0), nsteps, uN, ckpt=ck, ckpt_every=5)
+    assert st["steps"] == nsteps
+    assert np.linalg.norm(host(uN) - refs[-1]) <= 1e-8 * np.linalg.norm(refs[-1])
+    for q in range(ck.shape[0]):
+        assert np.linalg.norm(host(ck[q]) - refs[5 * q]) <= 1e-8 * np.linalg.norm(refs[5 * q])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_double_glazing_steps(prec):
+    mesh, prob = dg(48)
+    A, b, _ = obt.radau_iia(3)
+    h = 0.01
+    ctx, At = oracle_ctx(prob, A, "LD", h, amg_prec=prec, **AMG_OPTS)
+    u0 = np.zeros(prob.n)
+    refs, _ = oirk.IRKSolver(prob, A, b, h, kind=None).run(u0, 3, direct=True)
+    u = dev(u0)
+    for t in range(3):
+        out = torch.empty_like(u)
+        B().irk_step(ctx, u, out)
+        err = np.linalg.norm(host(out) - refs[t + 1]) / np.linalg.norm(refs[t + 1])
+        assert err < 1e-8, (prec, t, err)
+        u = out
+
+
+def test_stage_output_and_residual():
+    mesh, prob = heat(36)
+    A, b, _ = obt.radau_iia(5)
+    h = 1 / 64
+    ctx, _ = oracle_ctx(prob, A, "LD", h, amg_prec="f32", **AMG_OPTS)
+    u0 = synth.heat_u0(mesh)
+    u = dev(u0)
+    out = torch.empty_like(u)
+    k = torch.empty(5 * prob.n, dtype=torch.float64, device="cuda")
+    st = B().irk_step(ctx, u, out, k)
+    kk = host(k).reshape(5, -1)
+    rhs = oirk.stage_rhs(prob.F, prob.g, u0, 5)
+    r = rhs - oirk.apply_operator(prob.M, prob.F, A, h, kk)
+    assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(rhs)
+    assert np.allclose(host(out), u0 + h * b @ kk, rtol=0, atol=1e-15 * np.abs(u0).max())
+    assert st["resid"] <= 1e-10
+
+
+def test_edge_cases():
+    bnd = B()
+    from paper_2010_11377_gb300._abi import IrkError
+    # one unknown (N = 2), s = 1
+    mesh, prob = heat(2)
+    A, b, _ = obt.radau_iia(1)
+    ctx, _ = oracle_ctx(prob, A, "J", 0.1)
+    u = dev(np.array([1.0]))
+    out = torch.empty_like(u)
+    bnd.irk_step(ctx, u, out)
+    ref = oirk.IRKSolver(prob, A, b, 0.1, kind=None).step(np.array([1.0]), direct=True).u
+    assert abs(host(out)[0] - ref[0]) < 1e-12
+    # zero state -> zero stages, no iterations
+    mesh, prob = heat(20)
+    A, b, _ = obt.radau_iia(3)
+    ctx, _ = oracle_ctx(prob, A, "LD", 0.05)
+    z = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(z)
+    st = bnd.irk_step(ctx, z, out)
+    assert st["iterations"] == 0 and torch.count_nonzero(out) == 0
+    # iteration cap: NOT_CONVERGED is reported, the iterate is returned
+    ctx2, _ = oracle_ctx(prob, A, "J", 0.05, max_it=2)
+    with pytest.raises(IrkError) as ei:
+        bnd.irk_step(ctx2, dev(synth.heat_u0(mesh)), out)
+    assert ei.value.status == 4
+    # non-finite input
+    bad = dev(np.full(prob.n, np.nan))
+    with pytest.raises(IrkError) as ei:
+        bnd.irk_step(ctx, bad, out)
+    assert ei.value.status == 7
+    # invalid: wrong dtype / stage index
+    with pytest.raises(ValueError):
+        bnd.irk_step(ctx, z.float(), out)
+    with pytest.raises(IrkError):
+        bnd.irk_vcycle(ctx, 9, z, out)
+
+
+def test_adjoint_gradients():
+    """Checkpointed adjoint (C ABI) vs the oracle's discrete adjoint with exact
+    solves: dL/du0 and dL/dkappa to 1e-8."""
+    N, s, h, nsteps, every = 20, 3, 1 / 32, 6, 2
+    mesh = synth.structured_mesh(N)
+    kap = np.exp(synth.grf_log_kappa(mesh, seed=4))
+    prob = ofem.heat_problem(mesh, kappa=kap)
+    A, b, _ = obt.radau_iia(s)
+    meshd = dict(xy=mesh.xy, tri=mesh.tri, dof=mesh.dof)
+    ctx, _ = oracle_ctx(prob, A, "LD", h, amg_prec="f32", mesh=meshd, **AMG_OPTS)
+    u0 = synth.random_smooth_u0(mesh, seed=4)
+    d = 0.5 * u0
+    Ke = ofem.element_stiffness_unit(mesh.xy, mesh.tri)
+    sol = oirk.IRKSolver(prob, A, b, h, kind="LD", subsolve="direct")
+    gu, gk, L = oirk.adjoint_gradients(sol, Ke, mesh.dof[mesh.tri], u0, nsteps, d, direct=True)
+    bnd = B()
+    uN = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ck = torch.empty(nsteps // every, prob.n, dtype=torch.float64, device="cuda")
+    bnd.irk_run(ctx, dev(u0), nsteps, uN, ckpt=ck, ckpt_every=every)
+    lam = torch.empty_like(uN)
+    bnd.irk_apply_mass(ctx, uN - dev(d), lam)
+    grad = torch.zeros(mesh.n_tri, dtype=torch.float64, device="cuda")
+    bnd.irk_adjoint_run(ctx, ck, nsteps, every, lam, grad)
+    assert np.linalg.norm(host(lam) - gu) <= 1e-8 * np.linalg.norm(gu)
+    assert np.linalg.norm(host(grad) - gk) <= 1e-8 * np.linalg.norm(gk)
+    # set_kappa rebuilds F on the GPU: the forward run still matches
+    ctx2, _ = oracle_ctx(ofem.heat_problem(mesh), A, "LD", h, amg_prec="f32", mesh=meshd, **AMG_OPTS)
+    bnd.irk_set_kappa(ctx2, dev(kap))
+    uN2 = torch.empty_like(uN)
+    bnd.irk_run(ctx2, dev(u0), nsteps, uN2)
+    assert np.linalg.norm(host(uN2) - host(uN)) <= 1e-9 * np.linalg.norm(host(uN))
