@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark: IRK time steps of the 2D heat problem on a 1024 x 1024 grid
+(1,046,529 unknowns per stage), Radau IIA s = 5, h_t = 1/64, right-
+preconditioned FGMRES(30) to rtol 1e-10 with the block LDU preconditioner
+P_LD and one FP32 smoothed-aggregation V-cycle per diagonal block.
+
+Metric: stage-unknowns x steps / s  (s * n per time step).  A step is one full
+IRK time step: right-hand side, the whole preconditioned FGMRES solve, the
+update.  Inputs live in HBM; the working set (Krylov bases of 31 x 42 MB) is
+far larger than L2, so no flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own copy of the workload (independent
+problems, no data-path collective); value sums all ranks' work over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (grid N, stages s, h_t, preconditioner, AMG precision)
+    "heat1024_radau5_LD_f32amg": (1024, 5, 1.0 / 64, "LD", "f32"),
+    "heat256_radau5_LD_f32amg": (256, 5, 1.0 / 64, "LD", "f32"),
+    "heat32_radau2_LD_f32amg": (32, 2, 0.05, "LD", "f32"),
+}
+DEFAULT = "heat1024_radau5_LD_f32amg"
+METRIC = "stage-unknowns x steps / s (rtol 1e-10)"
+UNIT = "stage-unknowns*steps/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                mhz.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------------------
+def build_context(name, amg_prec=None):
+    import numpy as np  # noqa: F401
+    from paper_2010_11377_gb300 import binding as B
+    from paper_2010_11377_gb300 import problems
+    N, s, h, kind, prec = WORKLOADS[name]
+    prob = problems.heat(N)
+    A, b, c = B.irk_butcher_table("radau_iia", s)
+    opts = B.irk_default_options(kind=kind, amg_prec=amg_prec or prec)
+    t0 = time.perf_counter()
+    ctx = B.irk_setup(prob["rowptr"], prob["col"], prob["valM"], prob["valF"], (A, b, c), h, options=opts)
+    setup_s = time.perf_counter() - t0
+    return ctx, prob, setup_s
+
+
+def timed_steps(ctx, u, steps, warmup, dist=None):
+    import torch
+    from paper_2010_11377_gb300 import binding as B
+    out = torch.empty_like(u)
+    if warmup:
+        B.irk_run(ctx, u, warmup, out)
+        u = out.clone()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = B.irk_kernel_launches(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = B.irk_run(ctx, u, steps, out)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    return ms, st, B.irk_kernel_launches(ctx) - l0, out
+
+
+def e2e_steps(ctx, u_host, steps):
+    """Per step: pinned host u_n -> device, irk_step, u_{n+1} -> pinned host."""
+    import torch
+    from paper_2010_11377_gb300 import binding as B
+    n = u_host.numel()
+    hin = u_host.pin_memory()
+    hout = torch.empty(n, dtype=torch.float64).pin_memory()
+    dev_in = torch.empty(n, dtype=torch.float64, device="cuda")
+    dev_out = torch.empty_like(dev_in)
+    dev_in.copy_(hin, non_blocking=True)
+    B.irk_step(ctx, dev_in, dev_out)          # warm
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        dev_in.copy_(hin, non_blocking=True)
+        B.irk_step(ctx, dev_in, dev_out)
+        hout.copy_(dev_out, non_blocking=True)
+        hin, hout = hout, hin
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), 8 * n, 8 * n
+
+
+def roofline(ctx, s, its_per_step, traffic_file):
+    """Per-kernel timing (CUDA events on the library stream, standalone
+    replays on the buffers of the last solve) and the roofline of the kernel
+    with the largest time per step."""
+    from paper_2010_11377_gb300 import binding as B
+    pk, src = peaks()
+    fp64_peak_tflops = 1.25            # nominal GB300 FP64 (vector)
+    jm = max(1, min(29, int(round(its_per_step / 2))))   # mean basis index of an iteration
+    prof = {}
+    for tgt, j in (("kron", 0), ("precond", 0), ("vcycle", 0), ("smooth0", 0), ("gs_dots", jm), ("gs_axpy", jm)):
+        r = B.irk_profile(ctx, tgt, j=j, warm=3, reps=10)
+        r["GBps"] = r["bytes"] / (r["ms"] * 1e-3) / 1e9
+        r["TFLOPs"] = r["flops"] / (r["ms"] * 1e-3) / 1e12
+        prof[tgt] = r
+    per_step = {
+        "kron": prof["kron"]["ms"] * its_per_step,
+        "precond": prof["precond"]["ms"] * its_per_step,
+        "gram_schmidt": (prof["gs_dots"]["ms"] + prof["gs_axpy"]["ms"]) * its_per_step,
+    }
+    # single-kernel candidates: the operator apply (FP64, one launch per
+    # iteration), the finest smoothing step, the GS passes
+    kern = {"k_kron": prof["kron"], "k_gs_dots": prof["gs_dots"], "k_gs_axpy": prof["gs_axpy"]}
+    top = max(kern, key=lambda k: kern[k]["ms"])
+    t = kern[top]
+    hbm = pk["hbm_gbs"]
+    traffic = None
+    if traffic_file and os.path.exists(traffic_file):
+        for ln in open(traffic_file):
+            if ln.startswith(top + " traffic_bytes_per_launch:"):
+                v = ln.split(":", 1)[1].strip()
+                traffic = None if v == "null" else float(v)
+    # FP64 kernels on GB300 are bound by the FP64 pipe when flops/byte exceeds
+    # 1.25e12 / hbm; report the binding roof
+    ai = t["flops"] / t["bytes"]
+    ridge = fp64_peak_tflops * 1e12 / (hbm * 1e9)
+    if ai > ridge:
+        roof = {"bound": "alu", "achieved": t["TFLOPs"], "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": t["TFLOPs"] / fp64_peak_tflops, "traffic": traffic,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (GB300)", "kernel": top,
+                "hbm_achieved_GBps": t["GBps"], "hbm_frac_of_measured": t["GBps"] / hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": t["GBps"], "peak": hbm, "unit": "GB/s", "frac": t["GBps"] / hbm,
+                "traffic": traffic, "peak_source": f"{src} copy bandwidth", "kernel": top}
+    vc = prof["smooth0"]
+    extra = {"per_iteration_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
+             "per_step_ms_estimate": {k: round(v, 3) for k, v in per_step.items()},
+             "smooth0_hbm": {"achieved": round(vc["GBps"], 1), "peak": hbm, "frac": round(vc["GBps"] / hbm, 3)},
+             "precond_hbm": {"achieved": round(prof["precond"]["GBps"], 1),
+                             "frac": round(prof["precond"]["GBps"] / hbm, 3)},
+             "gs_mean_j": jm}
+    return roof, extra
+
+
+class OracleSample:
+    """The FP64 oracle as it stands on this host, set up once for a workload
+    (assembly and AMG hierarchies untimed); a sample runs a bounded number of
+    FGMRES iterations of one time step and scales the per-iteration time to
+    the iterations of a full step."""
+
+    def __init__(self, name):
+        import synth
+        from oracle import butcher as obt
+        from oracle import fem as ofem
+        from oracle import irk as oirk
+        N, s, h, kind, _ = WORKLOADS[name]
+        self.name, self.s = name, s
+        mesh = synth.structured_mesh(N)
+        prob = ofem.heat_problem(mesh)
+        A, b, _ = obt.radau_iia(s)
+        t0 = time.perf_counter()
+        self.pc = oirk.BlockPreconditioner(prob.M, prob.F, A, h, kind, "amg")
+        self.setup_s = time.perf_counter() - t0
+        self.n = mesh.n
+        self.rhs = oirk.stage_rhs(prob.F, prob.g, synth.heat_u0(mesh), s)
+        self.op = lambda z: oirk.apply_operator(prob.M, prob.F, A, h, z)  # noqa: E731
+        self.fgmres = oirk.fgmres
+
+    def full_step_iterations(self):
+        return self.fgmres(self.op, self.pc.apply, self.rhs).iterations
+
+    def sample(self, k, iterations_per_step):
+        t0 = time.perf_counter()
+        self.fgmres(self.op, self.pc.apply, self.rhs, max_it=k)
+        per_it = (time.perf_counter() - t0) / k
+        step_s = per_it * iterations_per_step
+        return self.s * self.n / step_s, per_it
+
+
+def host_threads():
+    try:
+        import threadpoolctl
+        return max([d.get("num_threads", 1) for d in threadpoolctl.threadpool_info()] + [1])
+    except Exception:
+        return 1
+
+
+def cpu_baseline(name, iterations_per_step, budget_s=20.0):
+    o = OracleSample(name)
+    _, t1 = o.sample(1, iterations_per_step)
+    k = int(max(1, min(iterations_per_step, budget_s // max(t1, 1e-3))))
+    value, per_it = o.sample(k, iterations_per_step)
+    return {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+            "sample": f"{name}: {k} FGMRES iterations of one time step (AMG setup {o.setup_s:.1f} s untimed), "
+                      f"per-iteration time x {iterations_per_step} iterations per step (the GPU run's count)",
+            "seconds_per_iteration": per_it}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import synth
+    dist = None
+    rank, world = 0, 1
+    if args.gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as td
+        rank = int(os.environ.get("RANK", 0))
+        world = int(os.environ.get("WORLD_SIZE", args.gpus))
+        local = int(os.environ.get("LOCAL_RANK", rank))
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl", rank=rank, world_size=world)
+        dist = td
+    from __graft_entry__ import build
+    build()
+    from paper_2010_11377_gb300 import binding as B
+
+    name = args.workload
+    N, s, h, kind, prec = WORKLOADS[name]
+    ctx, prob, setup_s = build_context(name)
+    u = torch.tensor(synth.heat_u0(prob["mesh"]), dtype=torch.float64, device="cuda")
+    n = prob["n"]
+    dev_index = torch.cuda.current_device()
+    with ClockSampler(dev_index) as clk:
+        ms, st, launches, uN = timed_steps(ctx, u, args.steps, args.warmup, dist)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * s * n * args.steps / (ms * 1e-3)
+    its = st["iterations"] / max(st["steps"], 1)
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded P1 heat problem; u0 = sin(pi x) sin(pi y))",
+        "config": {"workload": name, "grid": f"{N}x{N}", "n_per_stage": n, "stages": s, "method": "Radau IIA",
+                   "h_t": h, "precond": f"P_{kind}", "amg": prec + " V-cycle (Chebyshev 3, V(1,1))",
+                   "krylov": "FGMRES(30) rtol 1e-10", "parallelism": f"replicas x{world}",
+                   "l2": "working set > L2 (Krylov bases 1.3 GB); no flush"},
+        "iterations_per_step": its, "resid": st["resid"], "setup_s": setup_s,
+        "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    if args.launch_list:
+        print(json.dumps(out))
+        return
+    # end to end through the C ABI with host buffers
+    e2e_ms, bi, bo = e2e_steps(ctx, u.cpu(), max(2, args.steps // 2))
+    e2e_steps_n = max(2, args.steps // 2)
+    out["e2e"] = {"value": s * n * e2e_steps_n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+                  "d2h_bytes_per_step": bo}
+    # roofline of the dominant kernel
+    roof, extra = roofline(ctx, s, its, os.path.join(ROOT, "profiles", "ncu_traffic.txt"))
+    out["roofline"] = roof
+    out["kernels"] = extra
+    # FP64-AMG form of the same workload (the FP32-AMG speedup at equal accuracy)
+    if not args.no_fp64:
+        ctx.close()
+        ctx64, _, _ = build_context(name, amg_prec="f64")
+        k64 = max(2, args.steps // 2)
+        ms64, st64, _, u64 = timed_steps(ctx64, u, k64, 1)
+        out["fp64_amg"] = {"ms_per_step": ms64 / k64, "iterations_per_step": st64["iterations"] / k64,
+                           "speedup_of_f32_amg": (ms64 / k64) / (ms / args.steps), "resid": st64["resid"]}
+        ctx64.close()
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(name, max(1, int(round(its))))
+    print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle (the paper has no code) on the host cores,
+    same metric and workload.  Set-up and one full step (to count its FGMRES
+    iterations) are untimed; each timed step is a bounded sample of FGMRES
+    iterations scaled to that count."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    name = args.workload
+    o = OracleSample(name)
+    its = o.full_step_iterations()
+    per_step = []
+    k = 2
+    for i in range(args.warmup + args.steps):
+        v, _ = o.sample(k, its)
+        if i >= args.warmup:
+            per_step.append(1.0 / v)
+    value = 1.0 / (sum(per_step) / len(per_step))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * o.s * o.n / value, "higher_is_better": True,
+           "dtype": "f64", "data": "synthetic", "config": {"workload": name},
+           "cpu_baseline": {"kind": "oracle", "cores": host_threads(), "value": value,
+                            "sample": f"{name}: each step {k} FGMRES iterations of the oracle, scaled to the "
+                                      f"{its} iterations of its full step (setup {o.setup_s:.1f} s untimed)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="only the warm-up and timed steps (for an ncu launch list)")
+    args = ap.parse_args()
+    if args.launch_list:
+        args.no_cpu_baseline = args.no_fp64 = True
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

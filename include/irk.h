@@ -261,6 +261,21 @@ irk_status irk_amg_aggregates(irk_ctx* ctx, int32_t stage, int32_t level, int32_
 irk_status irk_amg_level_matrix(irk_ctx* ctx, int32_t stage, int32_t level, int64_t* rowptr,
                                 int32_t* col, double* val);
 
+/* Timing of one piece of an FGMRES iteration, replayed `reps` times on the
+ * context's stream between CUDA events after `warm` untimed launches, on the
+ * buffers of the last solve (their contents are overwritten; call it between
+ * solves).  which: IRK_PROF_KRON (w = A z_j, the operator apply as in the
+ * loop), IRK_PROF_VCYCLE (one V-cycle on the first diagonal block),
+ * IRK_PROF_PRECOND (the whole P^{-1} application), IRK_PROF_GS_DOTS and
+ * IRK_PROF_GS_AXPY (the two Gram-Schmidt passes at basis index j),
+ * IRK_PROF_SMOOTH0 (one finest-level Chebyshev step of the first block).
+ * *ms receives the mean time per replay, *bytes the algorithmic DRAM bytes
+ * of one replay and *flops its algorithmic floating-point operations. */
+enum { IRK_PROF_KRON = 0, IRK_PROF_VCYCLE = 1, IRK_PROF_PRECOND = 2, IRK_PROF_GS_DOTS = 3,
+       IRK_PROF_GS_AXPY = 4, IRK_PROF_SMOOTH0 = 5 };
+irk_status irk_profile(irk_ctx* ctx, int32_t which, int32_t j, int32_t warm, int32_t reps, double* ms,
+                       double* bytes, double* flops);
+
 /* Number of kernels the library has launched through this context so far
  * (graph-launched kernels included). */
 int64_t irk_kernel_launches(const irk_ctx* ctx);

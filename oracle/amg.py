@@ -19,8 +19,9 @@ reading fixed in the design notes, step by step:
   P          tentative piecewise constant P_t (entries 1), smoothed once:
              P = (I - omega D^{-1} A) P_t, omega = 4 / (3 rho),
              rho = max_i sum_j |a_ij| / |a_ii|.
-  coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max; the
-             coarsest level is solved directly (dense LU).
+  coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max or
+             coarsening stalls (the next level would keep more than 90% of the
+             rows); the coarsest level is solved directly (dense LU).
   smoother   l1-Jacobi x <- x + D_l1^{-1} (b - A x), D_l1 = diag(sum_j |a_ij|),
              or Chebyshev of degree k on the l1-scaled operator D_l1^{-1} A,
              whose spectrum lies in (0, 1] for symmetric A (D_l1 - A is
@@ -177,7 +178,7 @@ class Hierarchy:
             G = strength_graph(lev.A, theta)
             agg, _ = aggregate(G, lvl)
             nc = int(agg.max()) + 1
-            if nc >= lev.n:
+            if 10 * nc > 9 * lev.n:
                 break
             P, _ = smoothed_prolongator(lev.A, agg, nc)
             lev.P = P

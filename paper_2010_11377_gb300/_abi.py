@@ -70,6 +70,8 @@ SIGNATURES = [
     ("irk_amg_info", C.c_int, [C.c_void_p, C.c_int32, c_int32_p, c_int32_p, c_int64_p]),
     ("irk_amg_aggregates", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, c_int32_p]),
     ("irk_amg_level_matrix", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, c_int64_p, c_int32_p, c_double_p]),
+    ("irk_profile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, c_double_p, c_double_p,
+                              c_double_p]),
     ("irk_kernel_launches", C.c_int64, [C.c_void_p]),
     ("irk_destroy", None, [C.c_void_p]),
     ("irk_last_error", C.c_char_p, [C.c_void_p]),

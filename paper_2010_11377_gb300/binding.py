@@ -256,6 +256,18 @@ def irk_amg_level_matrix(ctx: Context, stage, level):
     return rp, col, val
 
 
+PROFILE_TARGETS = {"kron": 0, "vcycle": 1, "precond": 2, "gs_dots": 3, "gs_axpy": 4, "smooth0": 5}
+
+
+def irk_profile(ctx: Context, which: str, j: int = 0, warm: int = 3, reps: int = 20) -> dict:
+    ms = C.c_double(0.0)
+    by = C.c_double(0.0)
+    fl = C.c_double(0.0)
+    check(lib().irk_profile(ctx.ptr, PROFILE_TARGETS[which], int(j), int(warm), int(reps), C.byref(ms), C.byref(by),
+                            C.byref(fl)), ctx.ptr)
+    return {"ms": ms.value, "bytes": by.value, "flops": fl.value}
+
+
 def irk_kernel_launches(ctx: Context) -> int:
     return int(lib().irk_kernel_launches(ctx.ptr))
 

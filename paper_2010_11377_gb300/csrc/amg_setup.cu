@@ -15,8 +15,10 @@
 //              aggregate of its phase-1 strong neighbour of largest priority;
 //              aggregates numbered by increasing root index
 //   P          (I - omega D^{-1} A) P_tent, omega = 4/(3 max_i sum_j|a_ij|/|a_ii|)
-//   coarse     A_c = P^T A P by two deterministic SpGEMMs; the coarsest level
-//              is inverted densely (Gauss-Jordan, partial pivoting, FP64).
+//   coarse     A_c = P^T A P by two deterministic SpGEMMs, until n <= coarse_max
+//              or coarsening stalls (a level would keep > 90% of its rows);
+//              the coarsest level is inverted densely (Gauss-Jordan, partial
+//              pivoting, FP64).
 #include "irk_internal.cuh"
 
 #include <cmath>
@@ -212,29 +214,20 @@ __global__ void k_agg_phase2(int n, int level, const int* __restrict__ grp, cons
 // P row r: entries over aggregates J of the row's columns,
 // P[r,J] = delta(agg(r)==J) - omega * ((1/a_rr) * sum_{c in row, agg(c)=J} a_rc)
 // summed in increasing column order.  Row length is at most the row of A.
-constexpr int P_ROW_CAP = 128;
-
 __global__ void k_prolong_count(int n, const int* __restrict__ rp, const int* __restrict__ col,
-                                const int* __restrict__ agg, int* __restrict__ cnt, int* __restrict__ ovf) {
+                                const int* __restrict__ agg, int* __restrict__ cnt) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  int len = rp[r + 1] - rp[r];
-  if (len > P_ROW_CAP) {
-    atomicExch(ovf, 1);
-    cnt[r] = 0;
-    return;
-  }
-  int a[P_ROW_CAP];
   int u = 0;
   for (int k = rp[r]; k < rp[r + 1]; ++k) {
     int J = agg[col[k]];
     bool seen = false;
-    for (int q = 0; q < u; ++q)
-      if (a[q] == J) {
+    for (int q = rp[r]; q < k; ++q)
+      if (agg[col[q]] == J) {
         seen = true;
         break;
       }
-    if (!seen) a[u++] = J;
+    if (!seen) ++u;
   }
   cnt[r] = u;
 }
@@ -428,7 +421,8 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
   CK_LAUNCH();
   scan_exclusive(flag, rootid, n, st);
   int nc = rd(rootid + n, st);
-  if (nc >= n || nc == 0) return false;
+  // stop when coarsening stalls: the next level would keep more than 90% of the rows
+  if (nc == 0 || 10 * int64_t(nc) > 9 * int64_t(n)) return false;
 
   int* agg1 = tmp.get<int>(n);
   lev.agg = pool.get<int>(n);
@@ -441,11 +435,8 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
 
   // smoothed prolongator
   int* pcnt = tmp.get<int>(n + 1);
-  int* ovf = tmp.get<int>(1);
-  CK(cudaMemsetAsync(ovf, 0, sizeof(int), st));
-  k_prolong_count<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, lev.agg, pcnt, ovf);
+  k_prolong_count<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, lev.agg, pcnt);
   CK_LAUNCH();
-  if (rd(ovf, st)) fail(IRK_ERR_CAPACITY, "AMG level row longer than 128 entries");
   P.n = n;
   P.ncols = nc;
   P.rowptr = pool.get<int>(n + 1);

@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <vector>
 
@@ -156,7 +158,7 @@ static void destroy_graphs(Ctx& c) {
 // condition the last kernel of each iteration sets from the device state.
 static void build_graph(Ctx& c, bool adjoint) {
   Graph& G = c.graph[adjoint ? 1 : 0];
-  if (G.exec) return;
+  if (G.exec || c.host_loop) return;
   cudaStream_t st = c.stream;
   cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   cudaGraph_t graph;
@@ -202,6 +204,32 @@ static void build_graph(Ctx& c, bool adjoint) {
   G.conditional = true;
 }
 
+// One solve: the step graph, or (host loop) the same kernel sequence with the
+// loop condition read back on the host after every iteration.
+static void launch_solve(Ctx& c, bool adjoint) {
+  Graph& G = c.graph[adjoint ? 1 : 0];
+  if (!c.host_loop) {
+    CK(cudaGraphLaunch(G.exec, c.stream));
+    return;
+  }
+  cudaStream_t st = c.stream;
+  if (adjoint) rhs_adjoint_launch(c, c.lam, st);
+  else rhs_forward_launch(c, c.u, st);
+  int64_t k = 1;
+  for (int it = 0; it < c.max_it + 8; ++it) {
+    PrecondArgs pa{c.V, &c.st->j, c.N, c.st->sigma, c.Z, c.N, &c.st->done};
+    k += precond_launch(c, pa, adjoint, st);
+    k += fgmres_body_launch(c, adjoint, st);
+    CK(cudaMemcpyAsync(c.h_flag, &c.st->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*c.h_flag) break;
+  }
+  if (adjoint) adjoint_lambda_launch(c, c.lam, c.tmpn, st);
+  else stage_update_launch(c, c.u, st);
+  record_launch(c, st);
+  c.launches += k + 2;
+}
+
 static void reset_records(Ctx& c) { CK(cudaMemsetAsync(c.step_counter, 0, sizeof(int), c.stream)); }
 
 static void collect_stats(Ctx& c, int nsteps, irk_stats* out, irk_status* dev_status, int graph_idx) {
@@ -225,7 +253,7 @@ static void collect_stats(Ctx& c, int nsteps, irk_stats* out, irk_status* dev_st
     if (r.status != IRK_OK && *dev_status == IRK_OK) *dev_status = static_cast<irk_status>(r.status);
   }
   const Graph& G = c.graph[graph_idx];
-  c.launches += G.fixed_kernels * nsteps + G.body_kernels * its;
+  if (!c.host_loop) c.launches += G.fixed_kernels * nsteps + G.body_kernels * its;
   if (out) *out = s;
 }
 
@@ -240,7 +268,7 @@ static irk_status run_steps(Ctx& c, const double* u0, int nsteps, double* uout, 
     if (ckpt && every > 0 && t % every == 0)
       CK(cudaMemcpyAsync(ckpt + int64_t(t / every) * c.n, c.u, sizeof(double) * c.n, cudaMemcpyDeviceToDevice,
                          c.stream));
-    CK(cudaGraphLaunch(c.graph[0].exec, c.stream));
+    launch_solve(c, false);
     if (kout) CK(cudaMemcpyAsync(kout + int64_t(t) * c.N, c.x, sizeof(double) * c.N, cudaMemcpyDeviceToDevice,
                                  c.stream));
   }
@@ -257,7 +285,7 @@ static irk_status adjoint_one(Ctx& c, const double* lam_in, const double* u_n, c
                               double* grad, bool timed) {
   if (lam_in != c.lam)
     CK(cudaMemcpyAsync(c.lam, lam_in, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
-  CK(cudaGraphLaunch(c.graph[1].exec, c.stream));
+  launch_solve(c, true);
   if (grad) adjoint_grad_launch(c, u_n, k_n, grad, c.stream);
   CK(cudaMemcpyAsync(lam_out, c.tmpn, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
   (void)timed;
@@ -478,6 +506,9 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
       for (int64_t k = 0; k < M.nnz; ++k) col[k] = M.col[k];
       irk::setup_mesh(c, *prob, rp, col);
     }
+    const char* hl = std::getenv("IRK_HOST_LOOP");
+    c.host_loop = hl && std::atoi(hl) != 0;
+    CK(cudaMallocHost(&c.h_flag, sizeof(int)));
     irk::alloc_solver_buffers(c);
     irk::build_hierarchies(c);
     CK(cudaStreamSynchronize(c.stream));
@@ -501,7 +532,7 @@ irk_status irk_step(irk_ctx* h, const double* d_u_n, double* d_u_np1, double* d_
     CK(cudaMemcpyAsync(c.u, d_u_n, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
     irk::reset_records(c);
     CK(cudaEventRecord(c.ev_t0, c.stream));
-    CK(cudaGraphLaunch(c.graph[0].exec, c.stream));
+    irk::launch_solve(c, false);
     CK(cudaEventRecord(c.ev_t1, c.stream));
     if (d_k) CK(cudaMemcpyAsync(d_k, c.x, sizeof(double) * c.N, cudaMemcpyDeviceToDevice, c.stream));
     CK(cudaMemcpyAsync(d_u_np1, c.u, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
@@ -575,12 +606,12 @@ irk_status irk_adjoint_run(irk_ctx* h, const double* d_ckpt, int32_t nsteps, int
       for (int t = s0; t < s1; ++t) {
         CK(cudaMemcpyAsync(c.ustore + int64_t(t - s0) * c.n, c.u, sizeof(double) * c.n, cudaMemcpyDeviceToDevice,
                            c.stream));
-        CK(cudaGraphLaunch(c.graph[0].exec, c.stream));
+        irk::launch_solve(c, false);
         CK(cudaMemcpyAsync(c.kstore + int64_t(t - s0) * c.N, c.x, sizeof(double) * c.N, cudaMemcpyDeviceToDevice,
                            c.stream));
       }
       for (int t = s1 - 1; t >= s0; --t) {
-        CK(cudaGraphLaunch(c.graph[1].exec, c.stream));
+        irk::launch_solve(c, true);
         if (d_grad_kappa)
           irk::adjoint_grad_launch(c, c.ustore + int64_t(t - s0) * c.n, c.kstore + int64_t(t - s0) * c.N, d_grad_kappa,
                                    c.stream);
@@ -616,8 +647,10 @@ irk_status irk_adjoint_run(irk_ctx* h, const double* d_ckpt, int32_t nsteps, int
         if (r.status != IRK_OK && dev == IRK_OK) dev = static_cast<irk_status>(r.status);
       }
     }
-    c.launches += c.graph[0].fixed_kernels * fwd_steps + c.graph[0].body_kernels * its_f;
-    c.launches += c.graph[1].fixed_kernels * adj_steps + c.graph[1].body_kernels * its_a;
+    if (!c.host_loop) {
+      c.launches += c.graph[0].fixed_kernels * fwd_steps + c.graph[0].body_kernels * its_f;
+      c.launches += c.graph[1].fixed_kernels * adj_steps + c.graph[1].body_kernels * its_a;
+    }
     if (d_grad_kappa) c.launches += adj_steps;
     if (stats) *stats = s;
     irk::end_call(c);
@@ -742,6 +775,96 @@ irk_status irk_amg_level_matrix(irk_ctx* h, int32_t stage, int32_t level, int64_
   });
 }
 
+irk_status irk_profile(irk_ctx* h, int32_t which, int32_t j, int32_t warm, int32_t reps, double* ms, double* bytes,
+                       double* flops) {
+  if (!h || !ms || reps < 1 || warm < 0) return set_err(h, IRK_ERR_INVALID, "bad argument");
+  return guarded(h, [&] {
+    Ctx& c = h->c;
+    double B = 0.0, Fl = 0.0;
+    irk::GmresState* scratch = nullptr;
+    irk::GmresState host_state;
+    std::function<void()> prep = [] {};
+    std::function<void()> launch;
+    const irk::Hier& H0 = c.hiers[c.plan.hier[0]];
+    switch (which) {
+      case IRK_PROF_KRON: {
+        launch = [&] { irk::profile_kron_launch(c, c.stream); };
+        double zs = c.amg.amg_prec == 64 ? 8.0 : 4.0;
+        B = double(c.Mc.nnz) * 20.0 + double(c.N) * (zs + 8.0);
+        Fl = 2.0 * (2.0 * c.s * double(c.Mc.nnz) + double(c.s) * c.s * c.n);
+        break;
+      }
+      case IRK_PROF_VCYCLE: {
+        irk::vcycle_launch(H0, c.amg, c.sc, c.Z, nullptr, 0, 0, c.stream, &B, &Fl);   // accounting pass
+        launch = [&] { irk::vcycle_launch(H0, c.amg, c.sc, c.Z, nullptr, 0, 0, c.stream); };
+        break;
+      }
+      case IRK_PROF_PRECOND: {
+        irk::PrecondArgs pa{c.V, nullptr, 0, nullptr, c.Z, 0, nullptr, &B, &Fl};
+        irk::precond_launch(c, pa, false, c.stream);
+        irk::PrecondArgs pb{c.V, nullptr, 0, nullptr, c.Z, 0, nullptr};
+        launch = [&, pb] { irk::precond_launch(c, pb, false, c.stream); };
+        break;
+      }
+      case IRK_PROF_GS_DOTS:
+      case IRK_PROF_GS_AXPY: {
+        if (j < 0 || j + 1 > c.m) irk::fail(IRK_ERR_INVALID, "j out of range");
+        scratch = c.pool.get<irk::GmresState>(1);
+        std::memset(&host_state, 0, sizeof(host_state));
+        host_state.j = j;
+        host_state.m = irk::MAX_M;
+        host_state.max_it = 1 << 30;
+        host_state.rtol = 0.0;
+        host_state.bnorm = 1.0;
+        host_state.wnorm2 = 0.0;   // never reorthogonalise
+        for (int i = 0; i <= irk::MAX_M; ++i) host_state.sigma[i] = 1.0;
+        for (int i = 0; i <= j; ++i) host_state.H[j * (irk::MAX_M + 1) + i] = 1e-3;
+        host_state.g[0] = 1.0;
+        bool axpy = which == IRK_PROF_GS_AXPY;
+        prep = [&] {
+          CK(cudaMemcpyAsync(scratch, &host_state, sizeof(host_state), cudaMemcpyHostToDevice, c.stream));
+        };
+        launch = [&, axpy] { irk::profile_gs_launch(c, scratch, axpy, c.stream); };
+        double N = double(c.N);
+        B = axpy ? (j + 3) * N * 8.0 : (j + 2) * N * 8.0;
+        Fl = axpy ? 2.0 * (j + 2) * N : 2.0 * (j + 2) * N;
+        break;
+      }
+      case IRK_PROF_SMOOTH0: {
+        irk::smooth0_launch(H0, c.amg, c.sc, c.stream, &B, &Fl);
+        launch = [&] {
+          double b2, f2;
+          irk::smooth0_launch(H0, c.amg, c.sc, c.stream, &b2, &f2);
+        };
+        break;
+      }
+      default:
+        irk::fail(IRK_ERR_INVALID, "unknown profile target");
+    }
+    irk::begin_call(c);
+    for (int w = 0; w < warm; ++w) {
+      prep();
+      launch();
+    }
+    double total = 0.0;
+    for (int r = 0; r < reps; ++r) {
+      prep();
+      CK(cudaEventRecord(c.ev_t0, c.stream));
+      launch();
+      CK(cudaEventRecord(c.ev_t1, c.stream));
+      CK(cudaEventSynchronize(c.ev_t1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, c.ev_t0, c.ev_t1));
+      total += t;
+    }
+    irk::end_call(c);
+    if (scratch) c.pool.release(scratch);
+    *ms = total / reps;
+    if (bytes) *bytes = B;
+    if (flops) *flops = Fl;
+  });
+}
+
 int64_t irk_kernel_launches(const irk_ctx* h) { return h ? h->c.launches : 0; }
 
 void irk_destroy(irk_ctx* h) {
@@ -757,6 +880,7 @@ void irk_destroy(irk_ctx* h) {
   if (c.ev_t0) cudaEventDestroy(c.ev_t0);
   if (c.ev_t1) cudaEventDestroy(c.ev_t1);
   if (c.stream) cudaStreamDestroy(c.stream);
+  if (c.h_flag) cudaFreeHost(c.h_flag);
   delete h;
 }
 

@@ -276,6 +276,8 @@ struct Ctx {
 
   Graph graph[2];           // forward step, adjoint step
   int64_t launches = 0;
+  bool host_loop = false;   // IRK_HOST_LOOP=1: host-driven FGMRES loop (same kernels, no graph)
+  int* h_flag = nullptr;    // pinned host copy of GmresState::done
 };
 
 // ---------------------------------------------------------------------------
@@ -308,7 +310,10 @@ void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaS
 // V-cycle on hierarchy H: rhs in H.lv[0].b, result written to out (level-0 size,
 // V-cycle precision).  Returns the number of kernels launched.
 int vcycle_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, void* out_base,
-                  const int* jp, int64_t jstride, int64_t off, cudaStream_t st);
+                  const int* jp, int64_t jstride, int64_t off, cudaStream_t st, double* bytes = nullptr,
+                  double* flops = nullptr);
+void smooth0_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, cudaStream_t st, double* bytes,
+                    double* flops);
 
 // preconditioner z = P^{-1} (sigma_j V_j), stage by stage (Section 4.2)
 struct PrecondArgs {
@@ -319,6 +324,8 @@ struct PrecondArgs {
   void* Z;                  // base of Z (AMG precision)
   int64_t ldz;
   const int* skip;          // device flag: write zeros instead (nullptr: never)
+  double* bytes = nullptr;  // accumulated algorithmic bytes / flops (optional)
+  double* flops = nullptr;
 };
 int precond_launch(Ctx& c, const PrecondArgs& a, bool transpose, cudaStream_t st);
 
@@ -335,5 +342,7 @@ void adjoint_lambda_launch(Ctx& c, const double* lam_in, double* lam_out, cudaSt
 void adjoint_grad_launch(Ctx& c, const double* u_n, const double* k_n, double* grad, cudaStream_t st);
 void assemble_kappa_launch(Ctx& c, const double* kappa, double* Fval, cudaStream_t st);
 void convert_launch(const void* in, int in_prec, void* out, int out_prec, int64_t n, cudaStream_t st);
+void profile_kron_launch(Ctx& c, cudaStream_t st);
+void profile_gs_launch(Ctx& c, GmresState* scratch, bool axpy, cudaStream_t st);
 
 }  // namespace irk

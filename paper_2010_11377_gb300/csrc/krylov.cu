@@ -576,6 +576,33 @@ int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
   return launches;
 }
 
+// w = A z_0 with the same kernel, buffers and launch shape as the loop
+void profile_kron_launch(Ctx& c, cudaStream_t st) {
+  int n = c.n;
+  int64_t N = c.N;
+  unsigned G = row_grid(c);
+  bool z32 = c.amg.amg_prec != 64;
+  IRK_DISPATCH_S(c.s, {
+    if (z32)
+      k_kron<S, float, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+                                            JPtr<const float>{static_cast<const float*>(c.Z), nullptr, N, 0, 0},
+                                            JPtr<double>{c.V, nullptr, N, 1, 0}, c.K, nullptr, nullptr, nullptr);
+    else
+      k_kron<S, double, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+                                             JPtr<const double>{static_cast<const double*>(c.Z), nullptr, N, 0, 0},
+                                             JPtr<double>{c.V, nullptr, N, 1, 0}, c.K, nullptr, nullptr, nullptr);
+  });
+  CK_LAUNCH();
+}
+
+// one Gram-Schmidt pass on a scratch state (axpy: also the Givens update)
+void profile_gs_launch(Ctx& c, GmresState* scratch, bool axpy, cudaStream_t st) {
+  unsigned G = row_grid(c);
+  if (axpy) k_gs_axpy<0><<<G, BS, 0, st>>>(scratch, c.V, c.N, c.N, c.partials);
+  else k_gs_dots<0><<<G, BS, 0, st>>>(scratch, c.V, c.N, c.N, c.partials);
+  CK_LAUNCH();
+}
+
 void set_loop_condition_launch(Ctx& c, cudaGraphConditionalHandle h, cudaStream_t st) {
   k_loop_ctrl<<<1, 32, 0, st>>>(c.st, h);
   CK_LAUNCH();

@@ -381,10 +381,10 @@ constexpr int GEMM_CAP = 2048;        // products per row held in shared memory
 constexpr int GEMM_WARPS = 2;          // warps per block
 
 __global__ void k_gemm_rowcount(int n, const int* __restrict__ arp, const int* __restrict__ acol,
-                                const int* __restrict__ brp, int* __restrict__ ub) {
+                                const int* __restrict__ brp, int64_t* __restrict__ ub) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  int s = 0;
+  int64_t s = 0;
   for (int k = arp[r]; k < arp[r + 1]; ++k) {
     int c = acol[k];
     s += brp[c + 1] - brp[c];
@@ -399,8 +399,8 @@ __global__ void __launch_bounds__(GEMM_WARPS * 32)
 k_gemm_numeric(int n, const int* __restrict__ arp, const int* __restrict__ acol,
                const double* __restrict__ aval, const int* __restrict__ brp,
                const int* __restrict__ bcol, const double* __restrict__ bval,
-               const int* __restrict__ off, int* __restrict__ tcol, double* __restrict__ tval,
-               int* __restrict__ cnt, int* __restrict__ overflow) {
+               const int64_t* __restrict__ off, int* __restrict__ tcol, double* __restrict__ tval,
+               int* __restrict__ cnt, int* __restrict__ novf, int* __restrict__ ovf_rows) {
   extern __shared__ unsigned char smem[];
   int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem) + warp * GEMM_CAP;
@@ -412,11 +412,8 @@ k_gemm_numeric(int n, const int* __restrict__ arp, const int* __restrict__ acol,
   // pass over A row: products go to [pos, pos + nnz(B_k))
   int a0 = arp[r], a1 = arp[r + 1];
   for (int k = a0; k < a1; ++k) total += brp[acol[k] + 1] - brp[acol[k]];
-  if (total > GEMM_CAP) {
-    if (lane == 0) {
-      atomicExch(overflow, 1);
-      cnt[r] = 0;
-    }
+  if (total > GEMM_CAP) {     // long row: left to k_gemm_merge
+    if (lane == 0) ovf_rows[atomicAdd(novf, 1)] = r;
     return;
   }
   int pos = 0;
@@ -461,7 +458,7 @@ k_gemm_numeric(int n, const int* __restrict__ arp, const int* __restrict__ acol,
   }
   // segmented sum in sorted order (lane 0: rows are short)
   if (lane == 0) {
-    int o = off[r];
+    int64_t o = off[r];
     int u = 0;
     int i = 0;
     while (i < total) {
@@ -481,12 +478,66 @@ k_gemm_numeric(int n, const int* __restrict__ arp, const int* __restrict__ acol,
   }
 }
 
-__global__ void k_gemm_compact(int n, const int* __restrict__ off, const int* __restrict__ rp,
+// Long rows (more products than the shared-memory sort holds): one thread
+// merges a_rk B_k into the running sorted row for k in A-row order, in global
+// scratch.  Sums accumulate in the same generation order as the sorted path.
+__global__ void k_gemm_merge(int nrows, const int* __restrict__ rows, const int* __restrict__ arp,
+                             const int* __restrict__ acol, const double* __restrict__ aval,
+                             const int* __restrict__ brp, const int* __restrict__ bcol,
+                             const double* __restrict__ bval, const int64_t* __restrict__ off, int* __restrict__ tcol,
+                             double* __restrict__ tval, int* __restrict__ tcol2, double* __restrict__ tval2,
+                             int* __restrict__ cnt) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nrows) return;
+  int r = rows[q];
+  int64_t o = off[r];
+  int* ca = tcol + o;
+  double* va = tval + o;
+  int* cb = tcol2 + o;
+  double* vb = tval2 + o;
+  int len = 0;
+  for (int k = arp[r]; k < arp[r + 1]; ++k) {
+    int c = acol[k];
+    double av = aval[k];
+    int b0 = brp[c], b1 = brp[c + 1];
+    int i = 0, t = b0, u = 0;
+    while (i < len || t < b1) {
+      if (t >= b1 || (i < len && ca[i] < bcol[t])) {
+        cb[u] = ca[i];
+        vb[u] = va[i];
+        ++i;
+      } else if (i >= len || bcol[t] < ca[i]) {
+        cb[u] = bcol[t];
+        vb[u] = __dmul_rn(av, bval[t]);
+        ++t;
+      } else {
+        cb[u] = ca[i];
+        vb[u] = __dadd_rn(va[i], __dmul_rn(av, bval[t]));
+        ++i;
+        ++t;
+      }
+      ++u;
+    }
+    int* tc = ca; ca = cb; cb = tc;
+    double* tv = va; va = vb; vb = tv;
+    len = u;
+  }
+  if (ca != tcol + o) {
+    for (int i = 0; i < len; ++i) {
+      tcol[o + i] = ca[i];
+      tval[o + i] = va[i];
+    }
+  }
+  cnt[r] = len;
+}
+
+__global__ void k_gemm_compact(int n, const int64_t* __restrict__ off, const int* __restrict__ rp,
                                const int* __restrict__ tcol, const double* __restrict__ tval,
                                int* __restrict__ col, double* __restrict__ val) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  int o = off[r], b = rp[r], e = rp[r + 1];
+  int64_t o = off[r];
+  int b = rp[r], e = rp[r + 1];
   for (int k = b; k < e; ++k) {
     col[k] = tcol[o + (k - b)];
     val[k] = tval[o + (k - b)];
@@ -496,19 +547,24 @@ __global__ void k_gemm_compact(int n, const int* __restrict__ off, const int* __
 void csr_spgemm(const CsrD& A, const CsrD& B, CsrD& C, DevPool& pool, cudaStream_t st) {
   int n = A.n;
   Tmp tmp;
-  int* ub = tmp.get<int>(n + 1);
-  int* off = tmp.get<int>(n + 1);
+  int64_t* ub = tmp.get<int64_t>(n + 1);
+  int64_t* off = tmp.get<int64_t>(n + 1);
   if (n) {
     k_gemm_rowcount<<<(n + 255) / 256, 256, 0, st>>>(n, A.rowptr, A.col, B.rowptr, ub);
     CK_LAUNCH();
   }
-  scan_exclusive(ub, off, n, st);
-  int total = read_scalar(off + n, st);
+  scan_exclusive64(ub, off, n, st);
+  int64_t total = read_scalar(off + n, st);
+  // products are staged in device scratch (12 bytes each, twice for long rows)
+  if (total > (int64_t(1) << 30))
+    fail(IRK_ERR_CAPACITY, "Galerkin product has more than 2^30 partial products (AMG coarsening stalled); "
+                           "lower theta");
   int* tcol = tmp.get<int>(total > 0 ? total : 1);
   double* tval = tmp.get<double>(total > 0 ? total : 1);
   int* cnt = tmp.get<int>(n + 1);
-  int* ovf = tmp.get<int>(1);
-  CK(cudaMemsetAsync(ovf, 0, sizeof(int), st));
+  int* novf = tmp.get<int>(1);
+  int* ovf_rows = tmp.get<int>(n > 0 ? n : 1);
+  CK(cudaMemsetAsync(novf, 0, sizeof(int), st));
   size_t shm = (sizeof(unsigned long long) + sizeof(double)) * GEMM_CAP * GEMM_WARPS;
   static bool attr = false;
   if (!attr) {
@@ -518,11 +574,17 @@ void csr_spgemm(const CsrD& A, const CsrD& B, CsrD& C, DevPool& pool, cudaStream
   }
   if (n) {
     k_gemm_numeric<<<(n + GEMM_WARPS - 1) / GEMM_WARPS, GEMM_WARPS * 32, shm, st>>>(
-        n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, tcol, tval, cnt, ovf);
+        n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, off, tcol, tval, cnt, novf, ovf_rows);
     CK_LAUNCH();
   }
-  if (read_scalar(ovf, st))
-    fail(IRK_ERR_CAPACITY, "SpGEMM row has more than 2048 products (AMG operator too dense)");
+  int nlong = read_scalar(novf, st);
+  if (nlong > 0) {
+    int* tcol2 = tmp.get<int>(total > 0 ? total : 1);
+    double* tval2 = tmp.get<double>(total > 0 ? total : 1);
+    k_gemm_merge<<<(nlong + 63) / 64, 64, 0, st>>>(nlong, ovf_rows, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                   B.val, off, tcol, tval, tcol2, tval2, cnt);
+    CK_LAUNCH();
+  }
   int* rp = pool.get<int>(n + 1);
   scan_exclusive(cnt, rp, n, st);
   int nnz = read_scalar(rp + n, st);

@@ -168,6 +168,11 @@ __global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
 // ---------------------------------------------------------------------------
 // V-cycle driver (kernel sequence; captured into CUDA graphs by the caller)
 // ---------------------------------------------------------------------------
+// algorithmic DRAM bytes / flops of the kernels (each operand counted once)
+struct Cost {
+  double bytes = 0.0, flops = 0.0;
+};
+
 template <typename T, typename V0>
 struct VCycle {
   const Hier& H;
@@ -175,6 +180,13 @@ struct VCycle {
   const SmoothCoef& sc;
   cudaStream_t st;
   int launches = 0;
+  Cost cost;
+
+  template <typename V>
+  void count_matvec(const Level& L, int vec_reads, int vec_writes) {
+    cost.bytes += double(L.nnz) * (sizeof(int) + sizeof(V)) + double(L.n) * sizeof(T) * (vec_reads + vec_writes);
+    cost.flops += 2.0 * double(L.nnz) + 4.0 * L.n;
+  }
 
   template <typename V, int XM>
   void smooth(const Level& L, const T* xin, const T* din, T* xout, T* dout, int step, JPtr<T> out) {
@@ -182,6 +194,8 @@ struct VCycle {
                                                   static_cast<const T*>(L.b), xin, din, xout, dout,
                                                   T(sc.alpha[step]), T(sc.beta[step]), T(sc.beta[0]), out);
     ++launches;
+    // reads: x (or b, dinv for the implicit step), b, dinv, d_prev; writes x, d
+    count_matvec<V>(L, XM == XM_EXPLICIT ? (din ? 4 : 3) : 2, dout ? 2 : 1);
   }
 
   // returns the buffer holding the level's result (or nullptr if written to out)
@@ -200,6 +214,8 @@ struct VCycle {
       unsigned blocks = nblk(int64_t(nl) * 32);
       k_dense_mv<T><<<blocks, 256, 0, st>>>(nl, static_cast<const T*>(H.cinv), b, xb, out);
       ++launches;
+      cost.bytes += double(nl) * nl * sizeof(T) + 2.0 * nl * sizeof(T);
+      cost.flops += 2.0 * double(nl) * nl;
       return out.base ? nullptr : xb;
     }
     const int steps = sc.steps;
@@ -234,10 +250,13 @@ struct VCycle {
         k_resid<V, T, XM_EXPLICIT><<<nblk(L.n), 256, 0, st>>>(view<V>(L.As), static_cast<const T*>(L.dinv), b,
                                                               cur, beta0, rb);
       ++launches;
+      count_matvec<V>(L, 2, 1);
     }
     const Level& C = H.lv[l + 1];
     k_spmv<T><<<nblk(C.n), 256, 0, st>>>(view<T>(L.Rs), p.nu_pre > 0 ? rb : b, static_cast<T*>(C.b));
     ++launches;
+    cost.bytes += double(L.Rs.nnz_pad) * (sizeof(int) + sizeof(T)) + double(L.n + C.n) * sizeof(T);
+    cost.flops += 2.0 * double(L.Rs.nnz_pad);
     T* e = level<T>(l + 1, none);
     // ---- prolongation and correction
     if (p.nu_pre == 0) {
@@ -250,6 +269,8 @@ struct VCycle {
       k_prolong<T, false><<<nblk(L.n), 256, 0, st>>>(view<T>(L.Ps), e, cur, nullptr, nullptr, beta0);
     }
     ++launches;
+    cost.bytes += double(L.Ps.nnz_pad) * (sizeof(int) + sizeof(T)) + double(2 * L.n + C.n) * sizeof(T);
+    cost.flops += 2.0 * double(L.Ps.nnz_pad);
     // ---- post-smoothing
     int total = p.nu_post * steps;
     int q = 0;
@@ -273,22 +294,53 @@ struct VCycle {
 
 template <typename T, typename V0>
 static int run_vcycle(const Hier& H, const AmgParams& p, const SmoothCoef& sc, JPtr<T> out,
-                      cudaStream_t st) {
-  VCycle<T, V0> vc{H, p, sc, st, 0};
+                      cudaStream_t st, double* bytes, double* flops) {
+  VCycle<T, V0> vc{H, p, sc, st, 0, Cost{}};
   vc.template level<V0>(0, out);
   CK_LAUNCH();
+  if (bytes) *bytes += vc.cost.bytes;
+  if (flops) *flops += vc.cost.flops;
   return vc.launches;
 }
 
 int vcycle_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, void* out_base, const int* jp,
-                  int64_t jstride, int64_t off, cudaStream_t st) {
+                  int64_t jstride, int64_t off, cudaStream_t st, double* bytes, double* flops) {
   if (H.amg_prec == 64) {
     JPtr<double> o = jptr<double>(static_cast<double*>(out_base), jp, jstride, 0, off);
-    return run_vcycle<double, double>(H, p, sc, o, st);
+    return run_vcycle<double, double>(H, p, sc, o, st, bytes, flops);
   }
   JPtr<float> o = jptr<float>(static_cast<float*>(out_base), jp, jstride, 0, off);
-  if (H.amg_prec == 16) return run_vcycle<float, __nv_bfloat16>(H, p, sc, o, st);
-  return run_vcycle<float, float>(H, p, sc, o, st);
+  if (H.amg_prec == 16) return run_vcycle<float, __nv_bfloat16>(H, p, sc, o, st, bytes, flops);
+  return run_vcycle<float, float>(H, p, sc, o, st, bytes, flops);
+}
+
+// one explicit finest-level smoothing step (step index 1) of hierarchy H
+void smooth0_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, cudaStream_t st, double* bytes,
+                    double* flops) {
+  const Level& L = H.lv[0];
+  JPtr<float> n32 = jptr<float>(nullptr);
+  JPtr<double> n64 = jptr<double>(nullptr);
+  int step = sc.steps > 1 ? 1 : 0;
+  if (H.amg_prec == 64) {
+    VCycle<double, double> vc{H, p, sc, st, 0, Cost{}};
+    vc.template smooth<double, XM_EXPLICIT>(L, static_cast<double*>(L.x), static_cast<double*>(L.d),
+                                            static_cast<double*>(L.y), static_cast<double*>(L.d), step, n64);
+    *bytes = vc.cost.bytes;
+    *flops = vc.cost.flops;
+  } else if (H.amg_prec == 16) {
+    VCycle<float, __nv_bfloat16> vc{H, p, sc, st, 0, Cost{}};
+    vc.template smooth<__nv_bfloat16, XM_EXPLICIT>(L, static_cast<float*>(L.x), static_cast<float*>(L.d),
+                                                   static_cast<float*>(L.y), static_cast<float*>(L.d), step, n32);
+    *bytes = vc.cost.bytes;
+    *flops = vc.cost.flops;
+  } else {
+    VCycle<float, float> vc{H, p, sc, st, 0, Cost{}};
+    vc.template smooth<float, XM_EXPLICIT>(L, static_cast<float*>(L.x), static_cast<float*>(L.d),
+                                           static_cast<float*>(L.y), static_cast<float*>(L.d), step, n32);
+    *bytes = vc.cost.bytes;
+    *flops = vc.cost.flops;
+  }
+  CK_LAUNCH();
 }
 
 // ---------------------------------------------------------------------------
@@ -386,7 +438,15 @@ int precond_launch(Ctx& c, const PrecondArgs& a, bool transpose, cudaStream_t st
     }
     CK_LAUNCH();
     ++launches;
-    launches += vcycle_launch(H, c.amg, c.sc, a.Z, a.jp, a.ldz, int64_t(stage) * n, st);
+    if (a.bytes) {
+      const Sell& F = c.Fs;
+      double sv = f64 ? 8.0 : 4.0;
+      *a.bytes += double(c.Fc.nnz) * (4.0 + sv) * (cp.n > 0 ? 1 : 0) + double(n) * (8.0 + sv) +
+                  double(n) * sv * cp.n;
+      *a.flops += 2.0 * double(c.Fc.nnz) * cp.n + 2.0 * n * cp.n;
+      (void)F;
+    }
+    launches += vcycle_launch(H, c.amg, c.sc, a.Z, a.jp, a.ldz, int64_t(stage) * n, st, a.bytes, a.flops);
   }
   return launches;
 }
