@@ -245,6 +245,11 @@ irk_status irk_apply_precond(irk_ctx* ctx, const double* d_v, double* d_z, int32
 /* d_x = one V-cycle on diagonal block `stage` (0..s-1) applied to d_b (n). */
 irk_status irk_vcycle(irk_ctx* ctx, int32_t stage, const double* d_b, double* d_x);
 
+/* True residual norm of a stage block: *norm = ||d_b - (I (x) M + h_t A (x) F) d_k||_2
+ * (d_k, d_b: s*n device).  The per-block partial sums go to the context's
+ * scratch; the result is copied to the host double *norm. */
+irk_status irk_residual_norm(irk_ctx* ctx, const double* d_k, const double* d_b, double* norm);
+
 /* d_y = M d_x (n). */
 irk_status irk_apply_mass(irk_ctx* ctx, const double* d_x, double* d_y);
 

@@ -228,6 +228,12 @@ def irk_vcycle(ctx: Context, stage, b, x):
     check(lib().irk_vcycle(ctx.ptr, int(stage), _dev(b), _dev(x)), ctx.ptr)
 
 
+def irk_residual_norm(ctx: Context, k, b) -> float:
+    out = C.c_double(0.0)
+    check(lib().irk_residual_norm(ctx.ptr, _dev(k), _dev(b), C.byref(out)), ctx.ptr)
+    return out.value
+
+
 def irk_apply_mass(ctx: Context, x, y):
     check(lib().irk_apply_mass(ctx.ptr, _dev(x), _dev(y)), ctx.ptr)
 

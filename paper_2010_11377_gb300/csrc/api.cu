@@ -14,10 +14,6 @@
 
 extern "C" irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, double* kappa);
 
-struct irk_ctx {
-  irk::Ctx c;
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -717,6 +713,19 @@ irk_status irk_vcycle(irk_ctx* h, int32_t stage, const double* d_b, double* d_x)
     c.launches += 1 + irk::vcycle_launch(H, c.amg, c.sc, c.Z, nullptr, 0, 0, c.stream);
     irk::convert_launch(c.Z, prec, d_x, 64, c.n, c.stream);
     c.launches += 1;
+    irk::end_call(c);
+  });
+}
+
+irk_status irk_residual_norm(irk_ctx* h, const double* d_k, const double* d_b, double* norm) {
+  if (!h || !d_k || !d_b || !norm) return set_err(h, IRK_ERR_INVALID, "NULL argument");
+  return guarded(h, [&] {
+    Ctx& c = h->c;
+    irk::begin_call(c);
+    // scratch: the context's partial-sum buffer (gs_grid slots), result in tmpn[0]
+    irk::residual_norm_launch(c, d_k, d_b, c.partials, c.gs_grid, c.tmpn, c.stream);
+    c.launches += 2;
+    CK(cudaMemcpyAsync(norm, c.tmpn, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     irk::end_call(c);
   });
 }

@@ -343,6 +343,12 @@ void adjoint_grad_launch(Ctx& c, const double* u_n, const double* k_n, double* g
 void assemble_kappa_launch(Ctx& c, const double* kappa, double* Fval, cudaStream_t st);
 void convert_launch(const void* in, int in_prec, void* out, int out_prec, int64_t n, cudaStream_t st);
 void profile_kron_launch(Ctx& c, cudaStream_t st);
+void residual_norm_launch(Ctx& c, const double* k, const double* b, double* partials, int grid, double* out,
+                          cudaStream_t st);
 void profile_gs_launch(Ctx& c, GmresState* scratch, bool axpy, cudaStream_t st);
 
 }  // namespace irk
+
+struct irk_ctx {
+  irk::Ctx c;
+};

@@ -576,6 +576,64 @@ int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
   return launches;
 }
 
+// ||b - A k||_2: per-block partial sums of the squared residual, then one
+// block sums them in block order
+template <int S>
+__global__ void __launch_bounds__(BS)
+k_resid_partials(int n, SellView<double> Mv, const double* __restrict__ Fval, const double* __restrict__ k,
+                 const double* __restrict__ b, KronCoef K, double* __restrict__ partials) {
+  double nrm = 0.0;
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    double mz[S], fz[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      mz[i] = 0.0;
+      fz[i] = 0.0;
+    }
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = Mv.sptr[sl];
+    int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
+    for (int q = 0; q < wdt; ++q) {
+      int64_t idx = base + (int64_t(q) << 5) + lane;
+      int c = Mv.col[idx];
+      double m = Mv.val[idx];
+      double f = Fval[idx];
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        double zz = k[int64_t(i) * n + c];
+        mz[i] = fma(m, zz, mz[i]);
+        fz[i] = fma(f, zz, fz[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double wi = mz[i];
+#pragma unroll
+      for (int j = 0; j < S; ++j) wi = fma(K.a[i * MAX_S + j], fz[j], wi);
+      wi = b[int64_t(i) * n + r] - wi;
+      nrm = fma(wi, wi, nrm);
+    }
+  }
+  double v[1] = {nrm};
+  block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int count, double* __restrict__ out) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s = 0.0;
+  for (int q = 0; q < count; ++q) s += partials[q];
+  *out = sqrt(s);
+}
+
+void residual_norm_launch(Ctx& c, const double* k, const double* b, double* partials, int grid, double* out,
+                          cudaStream_t st) {
+  IRK_DISPATCH_S(c.s, {
+    k_resid_partials<S><<<grid, BS, 0, st>>>(c.n, view<double>(c.Ms), c.Fs.v64, k, b, c.K, partials);
+  });
+  k_sum_partials<<<1, 32, 0, st>>>(partials, grid, out);
+  CK_LAUNCH();
+}
+
 // w = A z_0 with the same kernel, buffers and launch shape as the loop
 void profile_kron_launch(Ctx& c, cudaStream_t st) {
   int n = c.n;

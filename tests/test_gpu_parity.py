@@ -257,6 +257,19 @@ def test_stage_output_and_residual():
     assert st["resid"] <= 1e-10
 
 
+def test_residual_norm():
+    """||b - A k|| through the C ABI against the oracle's operator."""
+    mesh, prob = heat(39)
+    A, b, _ = obt.radau_iia(4)
+    h = 1 / 64
+    ctx, _ = oracle_ctx(prob, A, "LD", h)
+    k = synth.random_stage_block(prob.n, 4, 21)
+    rhs = synth.random_stage_block(prob.n, 4, 22)
+    ref = np.linalg.norm(rhs - oirk.apply_operator(prob.M, prob.F, A, h, k))
+    got = B().irk_residual_norm(ctx, dev(k.ravel()), dev(rhs.ravel()))
+    assert abs(got - ref) <= 1e-13 * ref
+
+
 def test_edge_cases():
     bnd = B()
     from paper_2010_11377_gb300._abi import IrkError
