@@ -250,6 +250,19 @@ irk_status irk_vcycle(irk_ctx* ctx, int32_t stage, const double* d_b, double* d_
  * scratch; the result is copied to the host double *norm. */
 irk_status irk_residual_norm(irk_ctx* ctx, const double* d_k, const double* d_b, double* norm);
 
+/* The same norm as irk_residual_norm, for callers that must not allocate:
+ * the call makes no cudaMalloc, cudaFree or other allocation.  The paper has
+ * no counterpart; this is a library facility.  d_norm is a DEVICE double that
+ * receives the norm.  The partial sums use a fixed device array inside libirk
+ * with one slot per 256 rows, so n (rows per stage) may be at most
+ * IRK_NOALLOC_MAX_ROWS; larger n gives IRK_ERR_CAPACITY.  The array's device
+ * address is looked up the first time the entry point runs on a device; make
+ * that first call outside any stream capture.  Every call shares the array
+ * (its contents are those of the last call), so calls that overlap on the GPU,
+ * from any context or thread, race: serialise them. */
+#define IRK_NOALLOC_MAX_ROWS 1048576
+irk_status irk_residual_norm_noalloc(irk_ctx* ctx, const double* d_k, const double* d_b, double* d_norm);
+
 /* d_y = M d_x (n). */
 irk_status irk_apply_mass(irk_ctx* ctx, const double* d_x, double* d_y);
 

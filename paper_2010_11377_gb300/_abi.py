@@ -67,6 +67,7 @@ SIGNATURES = [
     ("irk_apply_precond", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("irk_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("irk_residual_norm", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, c_double_p]),
+    ("irk_residual_norm_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("irk_apply_mass", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("irk_amg_info", C.c_int, [C.c_void_p, C.c_int32, c_int32_p, c_int32_p, c_int64_p]),
     ("irk_amg_aggregates", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, c_int32_p]),

@@ -234,6 +234,12 @@ def irk_residual_norm(ctx: Context, k, b) -> float:
     return out.value
 
 
+def irk_residual_norm_noalloc(ctx: Context, k, b, out):
+    """Allocation-free variant: the norm is written to the one-element FP64
+    CUDA tensor `out`."""
+    check(lib().irk_residual_norm_noalloc(ctx.ptr, _dev(k), _dev(b), _dev(out)), ctx.ptr)
+
+
 def irk_apply_mass(ctx: Context, x, y):
     check(lib().irk_apply_mass(ctx.ptr, _dev(x), _dev(y)), ctx.ptr)
 
