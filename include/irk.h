@@ -134,8 +134,8 @@ irk_status irk_ldu(int32_t s, const double* A, double* L, double* D, double* U);
  * receives kappa_2(A~^{-1} A). */
 irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, double* kappa);
 
-/* Fill *opt with the defaults: P_LD, FP32 AMG, Chebyshev degree 3 on [0.1, 1],
- * V(1,1), theta 0.08, coarse_max 256, 12 levels, FGMRES(30), rtol 1e-10,
+/* Fill *opt with the defaults: P_LD, FP32 AMG, Chebyshev degree 4 on [0.1, 1],
+ * V(1,1), theta 0.08, coarse_max 1024, 12 levels, FGMRES(30), rtol 1e-10,
  * max_it 1000, selective reorthogonalisation. */
 void irk_default_options(irk_options* opt);
 

@@ -482,16 +482,9 @@ void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaS
     if (lev.n <= coarse_max || static_cast<int>(H.lv.size()) >= maxl) break;
     CsrD P, R, Ac;
     if (!coarsen(lev, l, p, P, R, Ac, pool, st)) break;
-    int want64 = p.amg_prec == 64;
-    int want32 = p.amg_prec != 64;
-    csr_to_sell(P, lev.Ps, want64, want32, 0, pool, st);
-    csr_to_sell(R, lev.Rs, want64, want32, 0, pool, st);
-    pool.release(P.rowptr);
-    pool.release(P.col);
-    pool.release(P.val);
-    pool.release(R.rowptr);
-    pool.release(R.col);
-    pool.release(R.val);
+    int pprec = p.amg_prec == 64 ? 64 : 32;
+    make_matT(P, lev.Pm, pprec, pool, st);
+    make_matT(R, lev.Rm, pprec, pool, st);
     Level nl;
     nl.A = Ac;
     nl.n = Ac.n;
@@ -508,10 +501,8 @@ void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaS
   // per-level SELL matrices, l1 inverse diagonals, work vectors
   for (size_t l = 0; l < H.lv.size(); ++l) {
     Level& L = H.lv[l];
-    int want64 = p.amg_prec == 64;
-    int want32 = p.amg_prec == 32 || (p.amg_prec == 16 && l > 0);
-    int want16 = p.amg_prec == 16 && l == 0;
-    csr_to_sell(L.A, L.As, want64, want32, want16, pool, st);
+    int aprec = p.amg_prec == 64 ? 64 : ((p.amg_prec == 16 && l == 0) ? 16 : 32);
+    make_matT(L.A, L.Am, aprec, pool, st);
     if (p.amg_prec == 64) {
       L.dinv = pool.get<double>(L.n > 0 ? L.n : 1);
       k_l1_inverse<<<nb(L.n), 256, 0, st>>>(L.n, L.A.rowptr, L.A.val, static_cast<double*>(L.dinv), nullptr);

@@ -372,12 +372,12 @@ void irk_default_options(irk_options* o) {
   o->Atilde = nullptr;
   o->amg_prec = IRK_AMG_F32;
   o->smoother = IRK_SMOOTH_CHEBYSHEV;
-  o->cheb_degree = 3;
+  o->cheb_degree = 4;
   o->cheb_lo = 0.1;
   o->nu_pre = 1;
   o->nu_post = 1;
   o->theta = 0.08;
-  o->coarse_max = 256;
+  o->coarse_max = 1024;
   o->max_levels = 12;
   o->restart = 30;
   o->rtol = 1e-10;

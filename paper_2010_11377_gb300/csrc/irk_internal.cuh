@@ -106,6 +106,36 @@ inline SellView<V> view(const Sell& s) {
   return SellView<V>{s.n, s.sptr, s.col, sell_vals<V>(s)};
 }
 
+// One operator of a V-cycle level in the V-cycle precision.  Short rows
+// (mean <= 12 entries): SELL-32, one thread per row.  Longer rows: CSR with
+// `lanes` threads per row (4..32) and a shuffle reduction, so a coarse
+// Galerkin row of a few hundred entries is not walked by a single thread.
+struct MatT {
+  int n = 0, ncols = 0;
+  int64_t nnz = 0;
+  int lanes = 1;
+  Sell sell;                 // lanes == 1
+  int* rowptr = nullptr;     // lanes > 1
+  int* col = nullptr;
+  void* val = nullptr;       // CSR values (V-cycle precision, or BF16)
+  int64_t stored() const { return lanes == 1 ? sell.nnz_pad : nnz; }
+};
+
+template <typename V>
+struct LMat {
+  int n;
+  const int64_t* __restrict__ sptr;
+  const int* __restrict__ rowptr;
+  const int* __restrict__ col;
+  const V* __restrict__ val;
+};
+
+template <typename V>
+inline LMat<V> lmat(const MatT& m) {
+  if (m.lanes == 1) return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell)};
+  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val)};
+}
+
 // ---------------------------------------------------------------------------
 // AMG hierarchy (one per distinct diagonal block M + h A~_jj F)
 // ---------------------------------------------------------------------------
@@ -113,8 +143,7 @@ struct Level {
   int n = 0;
   int64_t nnz = 0;
   CsrD A;                    // FP64 CSR as built (kept for export and rebuilds)
-  Sell As;                   // SELL values in the V-cycle precision
-  Sell Ps, Rs;               // prolongation n x nc, restriction nc x n
+  MatT Am, Pm, Rm;           // level operator, prolongation n x nc, restriction nc x n
   int* agg = nullptr;        // aggregate of every row (not on the coarsest level)
   void* dinv = nullptr;      // 1 / sum_j |a_ij|, V-cycle precision
   void *b = nullptr, *x = nullptr, *y = nullptr, *r = nullptr, *d = nullptr;
@@ -131,10 +160,10 @@ struct Hier {
 
 struct AmgParams {
   double theta = 0.08;
-  int coarse_max = 256;
+  int coarse_max = 1024;
   int max_levels = 12;
   int smoother = IRK_SMOOTH_CHEBYSHEV;
-  int cheb_degree = 3;
+  int cheb_degree = 4;
   double cheb_lo = 0.1;
   int nu_pre = 1, nu_post = 1;
   int amg_prec = 32;
@@ -298,6 +327,10 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
 void sell_share_pattern(const Sell& pat, const double* csr_vals, const CsrD& A, Sell& S, int want64,
                         int want32, DevPool& pool, cudaStream_t st);
 void csr_transpose(const CsrD& A, CsrD& T, DevPool& pool, cudaStream_t st);
+int choose_lanes(int64_t nnz, int n);
+// V-cycle operator in precision prec (64, 32, 16 = BF16) from an FP64 CSR that
+// stays alive (its index arrays are shared); force_lanes > 0 fixes the layout
+void make_matT(const CsrD& A, MatT& m, int prec, DevPool& pool, cudaStream_t st, int force_lanes = 0);
 void csr_spgemm(const CsrD& A, const CsrD& B, CsrD& C, DevPool& pool, cudaStream_t st);
 void csr_axpby_same_pattern(const CsrD& X, const double* valX, const double* valY, double c,
                             double* out, cudaStream_t st);   // out = X + c Y (no FMA)

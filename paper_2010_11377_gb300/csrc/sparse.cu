@@ -310,6 +310,52 @@ void sell_share_pattern(const Sell& pat, const double* csr_vals, const CsrD& A, 
 }
 
 // ---------------------------------------------------------------------------
+// V-cycle operator: SELL for short rows, CSR with lanes-per-row otherwise
+// ---------------------------------------------------------------------------
+__global__ void k_convert_vals(int64_t nnz, const double* __restrict__ in, double* __restrict__ v64,
+                               float* __restrict__ v32, __nv_bfloat16* __restrict__ v16) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= nnz) return;
+  double v = in[i];
+  if (v64) v64[i] = v;
+  if (v32) v32[i] = static_cast<float>(v);
+  if (v16) v16[i] = __double2bfloat16(v);
+}
+
+int choose_lanes(int64_t nnz, int n) {
+  double avg = n > 0 ? double(nnz) / n : 0.0;
+  if (avg <= 12.0) return 1;
+  if (avg <= 32.0) return 4;
+  if (avg <= 64.0) return 8;
+  if (avg <= 128.0) return 16;
+  return 32;
+}
+
+void make_matT(const CsrD& A, MatT& m, int prec, DevPool& pool, cudaStream_t st, int force_lanes) {
+  m.n = A.n;
+  m.ncols = A.ncols;
+  m.nnz = A.nnz;
+  m.lanes = force_lanes > 0 ? force_lanes : choose_lanes(A.nnz, A.n);
+  if (m.lanes == 1) {
+    csr_to_sell(A, m.sell, prec == 64, prec == 32, prec == 16, pool, st);
+    return;
+  }
+  m.rowptr = A.rowptr;
+  m.col = A.col;
+  int64_t nn = A.nnz > 0 ? A.nnz : 1;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  __nv_bfloat16* v16 = nullptr;
+  if (prec == 64) m.val = v64 = pool.get<double>(nn);
+  else if (prec == 32) m.val = v32 = pool.get<float>(nn);
+  else m.val = v16 = pool.get<__nv_bfloat16>(nn);
+  if (A.nnz) {
+    k_convert_vals<<<nblk(A.nnz), 256, 0, st>>>(A.nnz, A.val, v64, v32, v16);
+    CK_LAUNCH();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // transpose (counting sort, then each row sorted by column)
 // ---------------------------------------------------------------------------
 __global__ void k_count_cols(int64_t nnz, const int* __restrict__ col, int* __restrict__ cnt) {

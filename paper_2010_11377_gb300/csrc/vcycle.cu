@@ -45,28 +45,49 @@ SmoothCoef smooth_coefficients(const AmgParams& p) {
 // x^(0) implicit: x1 = beta0 * dinv * b
 enum { XM_EXPLICIT = 0, XM_IMPLICIT = 1, XM_ZERO = 2 };
 
+// Row product sum_c a_rc x(c) of operator A at row r (r < 0: an idle group
+// that only takes part in the shuffles).  L == 1: SELL-32, one thread per row;
+// L > 1: CSR, L consecutive lanes per row, strided over the row, reduced by an
+// xor-shuffle so every lane of the group holds the sum.
+template <int L, typename V, typename T, typename XF>
+__device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
+  T acc = T(0);
+  if (L == 1) {
+    if (r >= 0) {
+      int sl = r >> 5, ln = r & 31;
+      int64_t base = A.sptr[sl];
+      int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
+      for (int k = 0; k < w; ++k) {
+        int64_t idx = base + (int64_t(k) << 5) + ln;
+        acc = fma(widen(A.val[idx]), xf(A.col[idx]), acc);
+      }
+    }
+  } else {
+    if (r >= 0) {
+      int e = A.rowptr[r + 1];
+      for (int k = A.rowptr[r] + lane; k < e; k += L) acc = fma(widen(A.val[k]), xf(A.col[k]), acc);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
+  }
+  return acc;
+}
+
 // One smoothing step: d = alpha d_prev + beta D^{-1}(b - A x); x_out = x + d.
 // XM_IMPLICIT: x and d_prev are the implicit first step; XM_ZERO: x = 0, no product.
-template <typename V, typename T, int XM>
+template <typename V, typename T, int L, int XM>
 __global__ void __launch_bounds__(256)
-k_smooth(SellView<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ xin,
-         const T* din, T* __restrict__ xout, T* dout, T alpha, T beta, T beta0,
-         JPtr<T> out) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= A.n) return;
+k_smooth(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ xin,
+         const T* din, T* __restrict__ xout, T* dout, T alpha, T beta, T beta0, JPtr<T> out) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = gid / L, lane = gid % L;
+  bool valid = r < A.n;
   T ax = T(0);
-  if (XM != XM_ZERO) {
-    int sl = r >> 5, lane = r & 31;
-    int64_t base = A.sptr[sl];
-    int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-    for (int k = 0; k < w; ++k) {
-      int64_t idx = base + (int64_t(k) << 5) + lane;
-      int c = A.col[idx];
-      T v = widen(A.val[idx]);
-      T xc = (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : xin[c];
-      ax = fma(v, xc, ax);
-    }
-  }
+  if (XM != XM_ZERO)
+    ax = row_dot<L, V, T>(A, valid ? r : -1, lane, [&](int c) {
+      return (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : xin[c];
+    });
+  if (!valid || lane != 0) return;
   T dr = dinv[r], br = b[r];
   T xr, dprev;
   if (XM == XM_EXPLICIT) {
@@ -88,58 +109,39 @@ k_smooth(SellView<V> A, const T* __restrict__ dinv, const T* __restrict__ b, con
 }
 
 // r = b - A x  (x explicit or the implicit first step)
-template <typename V, typename T, int XM>
+template <typename V, typename T, int L, int XM>
 __global__ void __launch_bounds__(256)
-k_resid(SellView<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
-        T beta0, T* __restrict__ r_out) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= A.n) return;
-  int sl = r >> 5, lane = r & 31;
-  int64_t base = A.sptr[sl];
-  int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-  T ax = T(0);
-  for (int k = 0; k < w; ++k) {
-    int64_t idx = base + (int64_t(k) << 5) + lane;
-    int c = A.col[idx];
-    T xc = (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : x[c];
-    ax = fma(widen(A.val[idx]), xc, ax);
-  }
-  r_out[r] = b[r] - ax;
+k_resid(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x, T beta0,
+        T* __restrict__ r_out) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = gid / L, lane = gid % L;
+  bool valid = r < A.n;
+  T ax = row_dot<L, V, T>(A, valid ? r : -1, lane, [&](int c) {
+    return (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : x[c];
+  });
+  if (valid && lane == 0) r_out[r] = b[r] - ax;
 }
 
 // y = R x (restriction)
-template <typename T>
+template <typename T, int L>
 __global__ void __launch_bounds__(256)
-k_spmv(SellView<T> A, const T* __restrict__ x, T* __restrict__ y) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= A.n) return;
-  int sl = r >> 5, lane = r & 31;
-  int64_t base = A.sptr[sl];
-  int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-  T s = T(0);
-  for (int k = 0; k < w; ++k) {
-    int64_t idx = base + (int64_t(k) << 5) + lane;
-    s = fma(A.val[idx], x[A.col[idx]], s);
-  }
-  y[r] = s;
+k_spmv(LMat<T> A, const T* __restrict__ x, T* __restrict__ y) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = gid / L, lane = gid % L;
+  bool valid = r < A.n;
+  T s = row_dot<L, T, T>(A, valid ? r : -1, lane, [&](int c) { return x[c]; });
+  if (valid && lane == 0) y[r] = s;
 }
 
-// x += P e (prolongation and correction), x_implicit: x starts as beta0 dinv b
-template <typename T, bool IMPLICIT>
+// x += P e (prolongation and correction); IMPLICIT: x starts as beta0 dinv b
+template <typename T, int L, bool IMPLICIT>
 __global__ void __launch_bounds__(256)
-k_prolong(SellView<T> P, const T* __restrict__ e, T* x, const T* __restrict__ dinv,
-          const T* __restrict__ b, T beta0) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= P.n) return;
-  int sl = r >> 5, lane = r & 31;
-  int64_t base = P.sptr[sl];
-  int w = static_cast<int>((P.sptr[sl + 1] - base) >> 5);
-  T s = IMPLICIT ? beta0 * dinv[r] * b[r] : x[r];
-  for (int k = 0; k < w; ++k) {
-    int64_t idx = base + (int64_t(k) << 5) + lane;
-    s = fma(P.val[idx], e[P.col[idx]], s);
-  }
-  x[r] = s;
+k_prolong(LMat<T> P, const T* __restrict__ e, T* x, const T* __restrict__ dinv, const T* __restrict__ b, T beta0) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = gid / L, lane = gid % L;
+  bool valid = r < P.n;
+  T s = row_dot<L, T, T>(P, valid ? r : -1, lane, [&](int c) { return e[c]; });
+  if (valid && lane == 0) x[r] = (IMPLICIT ? beta0 * dinv[r] * b[r] : x[r]) + s;
 }
 
 // coarsest level: x = A^{-1} b with the stored dense inverse; one warp per row
@@ -164,6 +166,19 @@ __global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) out.get()[r] = src[r];
 }
+
+// dispatch on the lanes-per-row of an operator
+#define IRK_DISPATCH_L(LANES, ...)                          \
+  switch (LANES) {                                          \
+    case 1: { constexpr int LN = 1; __VA_ARGS__; } break;    \
+    case 4: { constexpr int LN = 4; __VA_ARGS__; } break;    \
+    case 8: { constexpr int LN = 8; __VA_ARGS__; } break;    \
+    case 16: { constexpr int LN = 16; __VA_ARGS__; } break;  \
+    case 32: { constexpr int LN = 32; __VA_ARGS__; } break;  \
+    default: fail(IRK_ERR_INVALID, "bad lanes per row");    \
+  }
+
+static inline unsigned grid_for(const MatT& m) { return nblk(int64_t(m.n) * m.lanes); }
 
 // ---------------------------------------------------------------------------
 // V-cycle driver (kernel sequence; captured into CUDA graphs by the caller)
@@ -190,9 +205,12 @@ struct VCycle {
 
   template <typename V, int XM>
   void smooth(const Level& L, const T* xin, const T* din, T* xout, T* dout, int step, JPtr<T> out) {
-    k_smooth<V, T, XM><<<nblk(L.n), 256, 0, st>>>(view<V>(L.As), static_cast<const T*>(L.dinv),
-                                                  static_cast<const T*>(L.b), xin, din, xout, dout,
-                                                  T(sc.alpha[step]), T(sc.beta[step]), T(sc.beta[0]), out);
+    LMat<V> A = lmat<V>(L.Am);
+    IRK_DISPATCH_L(L.Am.lanes, {
+      k_smooth<V, T, LN, XM><<<grid_for(L.Am), 256, 0, st>>>(A, static_cast<const T*>(L.dinv),
+                                                           static_cast<const T*>(L.b), xin, din, xout, dout,
+                                                           T(sc.alpha[step]), T(sc.beta[step]), T(sc.beta[0]), out);
+    });
     ++launches;
     // reads: x (or b, dinv for the implicit step), b, dinv, d_prev; writes x, d
     count_matvec<V>(L, XM == XM_EXPLICIT ? (din ? 4 : 3) : 2, dout ? 2 : 1);
@@ -243,34 +261,42 @@ struct VCycle {
     // ---- residual and restriction
     const T beta0 = T(sc.beta[0]);
     if (p.nu_pre > 0) {
-      if (implicit)
-        k_resid<V, T, XM_IMPLICIT><<<nblk(L.n), 256, 0, st>>>(view<V>(L.As), static_cast<const T*>(L.dinv), b,
-                                                              nullptr, beta0, rb);
-      else
-        k_resid<V, T, XM_EXPLICIT><<<nblk(L.n), 256, 0, st>>>(view<V>(L.As), static_cast<const T*>(L.dinv), b,
-                                                              cur, beta0, rb);
+      LMat<V> A = lmat<V>(L.Am);
+      const T* dv = static_cast<const T*>(L.dinv);
+      IRK_DISPATCH_L(L.Am.lanes, {
+        if (implicit)
+          k_resid<V, T, LN, XM_IMPLICIT><<<grid_for(L.Am), 256, 0, st>>>(A, dv, b, nullptr, beta0, rb);
+        else
+          k_resid<V, T, LN, XM_EXPLICIT><<<grid_for(L.Am), 256, 0, st>>>(A, dv, b, cur, beta0, rb);
+      });
       ++launches;
       count_matvec<V>(L, 2, 1);
     }
     const Level& C = H.lv[l + 1];
-    k_spmv<T><<<nblk(C.n), 256, 0, st>>>(view<T>(L.Rs), p.nu_pre > 0 ? rb : b, static_cast<T*>(C.b));
-    ++launches;
-    cost.bytes += double(L.Rs.nnz_pad) * (sizeof(int) + sizeof(T)) + double(L.n + C.n) * sizeof(T);
-    cost.flops += 2.0 * double(L.Rs.nnz_pad);
-    T* e = level<T>(l + 1, none);
-    // ---- prolongation and correction
-    if (p.nu_pre == 0) {
-      CK(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, st));
-      k_prolong<T, false><<<nblk(L.n), 256, 0, st>>>(view<T>(L.Ps), e, cur, nullptr, nullptr, beta0);
-    } else if (implicit) {
-      k_prolong<T, true><<<nblk(L.n), 256, 0, st>>>(view<T>(L.Ps), e, cur, static_cast<const T*>(L.dinv), b,
-                                                    beta0);
-    } else {
-      k_prolong<T, false><<<nblk(L.n), 256, 0, st>>>(view<T>(L.Ps), e, cur, nullptr, nullptr, beta0);
+    {
+      LMat<T> R = lmat<T>(L.Rm);
+      const T* src = p.nu_pre > 0 ? rb : b;
+      IRK_DISPATCH_L(L.Rm.lanes, { k_spmv<T, LN><<<grid_for(L.Rm), 256, 0, st>>>(R, src, static_cast<T*>(C.b)); });
     }
     ++launches;
-    cost.bytes += double(L.Ps.nnz_pad) * (sizeof(int) + sizeof(T)) + double(2 * L.n + C.n) * sizeof(T);
-    cost.flops += 2.0 * double(L.Ps.nnz_pad);
+    cost.bytes += double(L.Rm.nnz) * (sizeof(int) + sizeof(T)) + double(L.n + C.n) * sizeof(T);
+    cost.flops += 2.0 * double(L.Rm.nnz);
+    T* e = level<T>(l + 1, none);
+    // ---- prolongation and correction
+    {
+      LMat<T> P = lmat<T>(L.Pm);
+      const T* dv = static_cast<const T*>(L.dinv);
+      if (p.nu_pre == 0) CK(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, st));
+      IRK_DISPATCH_L(L.Pm.lanes, {
+        if (p.nu_pre > 0 && implicit)
+          k_prolong<T, LN, true><<<grid_for(L.Pm), 256, 0, st>>>(P, e, cur, dv, b, beta0);
+        else
+          k_prolong<T, LN, false><<<grid_for(L.Pm), 256, 0, st>>>(P, e, cur, nullptr, nullptr, beta0);
+      });
+    }
+    ++launches;
+    cost.bytes += double(L.Pm.nnz) * (sizeof(int) + sizeof(T)) + double(2 * L.n + C.n) * sizeof(T);
+    cost.flops += 2.0 * double(L.Pm.nnz);
     // ---- post-smoothing
     int total = p.nu_post * steps;
     int q = 0;
