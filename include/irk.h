@@ -229,6 +229,32 @@ irk_status irk_adjoint_run(irk_ctx* ctx, const double* d_ckpt, int32_t nsteps, i
 irk_status irk_set_kappa(irk_ctx* ctx, const double* d_kappa);
 
 /* ------------------------------------------------------------------------- *
+ * Batched instances: independent problems of different sizes advanced by one *
+ * CUDA graph launch (each instance a concurrent chain of the graph, its time *
+ * loop and FGMRES loop device-driven WHILE nodes).                           *
+ * ------------------------------------------------------------------------- */
+typedef struct irk_batch irk_batch;
+
+/* Build the batch over `count` contexts (same device; they must outlive the
+ * batch and must not be used concurrently with it).  Instance q runs nsteps
+ * IRK steps from d_u0[q] (n_q) into d_uN[q] (n_q), storing u every
+ * ckpt_every steps in d_ckpt[q] (ceil(nsteps/ckpt_every) x n_q).  If d_lambda
+ * is not NULL the adjoint graph is built too: irk_batch_adjoint then runs the
+ * checkpointed reverse sweep of every instance (as irk_adjoint_run), with
+ * d_lambda[q] (n_q) holding dL/du_N on entry and dL/du_0 on exit, and adds
+ * dL/dkappa into d_grad_kappa[q] (n_tri_q) when d_grad_kappa and its entry are
+ * not NULL.  All buffers are caller-owned device memory bound at creation. */
+irk_status irk_batch_create(irk_ctx* const* ctxs, int32_t count, int32_t nsteps, int32_t ckpt_every,
+                            const double* const* d_u0, double* const* d_uN, double* const* d_ckpt,
+                            double* const* d_lambda, double* const* d_grad_kappa, irk_batch** out);
+/* One graph launch: every instance forward.  stats (count entries, may be NULL)
+ * receive per-instance statistics; *ms (may be NULL) the device time. */
+irk_status irk_batch_run(irk_batch* b, void* stream, irk_stats* stats, double* ms);
+/* One graph launch: every instance's checkpointed adjoint sweep. */
+irk_status irk_batch_adjoint(irk_batch* b, void* stream, irk_stats* stats, double* ms);
+void irk_batch_destroy(irk_batch* b);
+
+/* ------------------------------------------------------------------------- *
  * Single operations (each one kernel sequence; used by tests and callers     *
  * composing their own iterations).                                           *
  * ------------------------------------------------------------------------- */

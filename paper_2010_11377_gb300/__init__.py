@@ -7,9 +7,9 @@ The compute path is libirk.so (hand-written CUDA for sm_103a behind the C ABI
 of include/irk.h); this package is its Python binding."""
 
 from .binding import (  # noqa: F401
-    Context, irk_adjoint_run, irk_adjoint_step, irk_amg_aggregates, irk_amg_info,
+    Batch, Context, irk_adjoint_run, irk_adjoint_step, irk_amg_aggregates, irk_amg_info,
     irk_amg_level_matrix, irk_apply_mass, irk_apply_operator, irk_apply_precond,
-    irk_atilde, irk_butcher_table, irk_default_options, irk_destroy, irk_fem_assemble,
+    irk_atilde, irk_batch_adjoint, irk_batch_create, irk_batch_destroy, irk_batch_run, irk_butcher_table, irk_default_options, irk_destroy, irk_fem_assemble,
     irk_fem_quad_points, irk_kernel_launches, irk_ldu, irk_profile, irk_residual_norm, irk_run, irk_set_kappa, irk_setup,
     irk_step, irk_vcycle,
 )

@@ -63,6 +63,12 @@ SIGNATURES = [
     ("irk_adjoint_run", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                   C.POINTER(IrkStats)]),
     ("irk_set_kappa", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("irk_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_int32,
+                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    ("irk_batch_run", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(IrkStats), c_double_p]),
+    ("irk_batch_adjoint", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(IrkStats), c_double_p]),
+    ("irk_batch_destroy", None, [C.c_void_p]),
     ("irk_apply_operator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("irk_apply_precond", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("irk_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),

@@ -212,6 +212,65 @@ def irk_adjoint_run(ctx: Context, ckpt, nsteps, ckpt_every, lam, grad_kappa=None
     return st.as_dict()
 
 
+class Batch:
+    """An irk_batch and the tensors it is bound to."""
+
+    def __init__(self, handle, ctxs, tensors):
+        self.handle = handle
+        self.ctxs = ctxs
+        self.tensors = tensors
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().irk_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_array(ts):
+    return (C.c_void_p * len(ts))(*[C.c_void_p(t.data_ptr()) if t is not None else None for t in ts])
+
+
+def irk_batch_create(ctxs, nsteps, ckpt_every, u0s, uNs, ckpts, lambdas=None, grads=None) -> Batch:
+    for t in list(u0s) + list(uNs) + list(ckpts) + list(lambdas or []) + [g for g in (grads or []) if g is not None]:
+        _dev(t)
+    n = len(ctxs)
+    handles = (C.c_void_p * n)(*[c.ptr for c in ctxs])
+    out = C.c_void_p()
+    lam = _ptr_array(lambdas) if lambdas is not None else None
+    gr = _ptr_array(grads) if grads is not None else None
+    check(lib().irk_batch_create(handles, n, int(nsteps), int(ckpt_every), _ptr_array(u0s), _ptr_array(uNs),
+                                 _ptr_array(ckpts), lam, gr, C.byref(out)))
+    return Batch(out, list(ctxs), [u0s, uNs, ckpts, lambdas, grads])
+
+
+def _batch_call(fn, b, stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    stats = (IrkStats * len(b.ctxs))()
+    ms = C.c_double(0.0)
+    check(fn(b.handle, C.c_void_p(stream.cuda_stream), stats, C.byref(ms)))
+    return [s.as_dict() for s in stats], ms.value
+
+
+def irk_batch_run(b: Batch, stream=None):
+    return _batch_call(lib().irk_batch_run, b, stream)
+
+
+def irk_batch_adjoint(b: Batch, stream=None):
+    return _batch_call(lib().irk_batch_adjoint, b, stream)
+
+
+def irk_batch_destroy(b: Batch):
+    b.close()
+
+
 def irk_set_kappa(ctx: Context, kappa):
     check(lib().irk_set_kappa(ctx.ptr, _dev(kappa)), ctx.ptr)
 

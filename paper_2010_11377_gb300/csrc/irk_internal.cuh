@@ -373,6 +373,8 @@ void kron_apply_plain(Ctx& c, const double* z, double* w, bool transpose, cudaSt
 void mass_apply_launch(Ctx& c, const double* x, double* y, cudaStream_t st);
 void adjoint_lambda_launch(Ctx& c, const double* lam_in, double* lam_out, cudaStream_t st);
 void adjoint_grad_launch(Ctx& c, const double* u_n, const double* k_n, double* grad, cudaStream_t st);
+void adjoint_grad_launch_at(Ctx& c, const double* u_base, const double* k_base, const int* step, double* grad,
+                            cudaStream_t st);
 void assemble_kappa_launch(Ctx& c, const double* kappa, double* Fval, cudaStream_t st);
 void convert_launch(const void* in, int in_prec, void* out, int out_prec, int64_t n, cudaStream_t st);
 void profile_kron_launch(Ctx& c, cudaStream_t st);

@@ -458,8 +458,10 @@ k_adj_lambda(int n, SellView<double> Fv, const double* __restrict__ mu, const do
 template <int S>
 __global__ void __launch_bounds__(BS)
 k_adj_grad(int n_tri, const int* __restrict__ tri, const int* __restrict__ dof, const double* __restrict__ Ke,
-           KronCoef K, int n, const double* __restrict__ u, const double* __restrict__ kst,
-           const double* __restrict__ mu, double* __restrict__ grad) {
+           KronCoef K, int n, JPtr<const double> up, JPtr<const double> kp, const double* __restrict__ mu,
+           double* __restrict__ grad) {
+  const double* __restrict__ u = up.get();
+  const double* __restrict__ kst = kp.get();
   for (int e = blockIdx.x * BS + threadIdx.x; e < n_tri; e += gridDim.x * BS) {
     int d[3];
 #pragma unroll
@@ -719,8 +721,16 @@ void adjoint_lambda_launch(Ctx& c, const double* lam_in, double* lam_out, cudaSt
 }
 
 void adjoint_grad_launch(Ctx& c, const double* u_n, const double* k_n, double* grad, cudaStream_t st) {
+  adjoint_grad_launch_at(c, u_n, k_n, nullptr, grad, st);
+}
+
+// u_n and k_n at u_base + (*step) n and k_base + (*step) s n (step == nullptr: offset 0)
+void adjoint_grad_launch_at(Ctx& c, const double* u_base, const double* k_base, const int* step, double* grad,
+                            cudaStream_t st) {
+  JPtr<const double> up{u_base, step, int64_t(c.n), 0, 0};
+  JPtr<const double> kp{k_base, step, c.N, 0, 0};
   IRK_DISPATCH_S(c.s, {
-    k_adj_grad<S><<<row_grid(c), BS, 0, st>>>(c.n_tri, c.tri, c.dof, c.Ke, c.K, c.n, u_n, k_n, c.x, grad);
+    k_adj_grad<S><<<row_grid(c), BS, 0, st>>>(c.n_tri, c.tri, c.dof, c.Ke, c.K, c.n, up, kp, c.x, grad);
   });
   CK_LAUNCH();
 }
