@@ -5,9 +5,12 @@ by one AMG V-cycle (Section 4.2) using smoothed aggregation from IFISS
 (Section 5).  The paper gives no further parameters; this module follows the
 reading fixed in the design notes, step by step:
 
-  strength   i ~ j strong iff  (|a_ij| + |a_ji|)/2 >= theta sqrt(|a_ii a_jj|)
+  strength   i ~ j strong iff  (|a_ij| + |a_ji|)/2 >= theta_l sqrt(|a_ii a_jj|)
              (symmetrised so that nonsymmetric blocks give an undirected
-             graph; theta = 0.08 by default).
+             graph); theta_l starts at theta (0.08) on every level and is
+             halved, at most 6 times, while more than a quarter of the level's
+             nodes have no strong coupling (isotropic or mass-dominated blocks
+             whose couplings all sit just below the threshold).
   roots      a maximal distance-2 independent set of the strength graph,
              chosen greedily in decreasing priority; priority of node i on
              level l is the 64-bit key (fmix32(i ^ (0x9E3779B9*(l+1))) << 32) | i
@@ -21,7 +24,9 @@ reading fixed in the design notes, step by step:
              rho = max_i sum_j |a_ij| / |a_ii|.
   coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max (1024) or
              coarsening stalls (the next level would keep more than 90% of the
-             rows); the coarsest level is solved directly (dense LU).
+             rows); the coarsest level is solved directly (dense LU) when it
+             has at most coarse_max rows, otherwise by 4 smoothing sweeps from
+             zero.
   smoother   l1-Jacobi x <- x + D_l1^{-1} (b - A x), D_l1 = diag(sum_j |a_ij|),
              or Chebyshev of degree k on the l1-scaled operator D_l1^{-1} A,
              whose spectrum lies in (0, 1] for symmetric A (D_l1 - A is
@@ -175,7 +180,13 @@ class Hierarchy:
             lvl = len(self.levels) - 1
             if lev.n <= coarse_max or len(self.levels) >= max_levels:
                 break
-            G = strength_graph(lev.A, theta)
+            th = theta
+            G = strength_graph(lev.A, th)
+            for _ in range(6):
+                if 4 * int(np.sum(np.diff(G.indptr) == 0)) <= lev.n:
+                    break
+                th *= 0.5
+                G = strength_graph(lev.A, th)
             agg, _ = aggregate(G, lvl)
             nc = int(agg.max()) + 1
             if 10 * nc > 9 * lev.n:
@@ -187,7 +198,9 @@ class Hierarchy:
             Ac = (lev.R @ lev.A @ P).tocsr()
             self.levels.append(Level(Ac))
         last = self.levels[-1]
-        last.lu = sla.lu_factor(last.A.toarray())
+        self.coarse_max = coarse_max
+        if last.n <= coarse_max:
+            last.lu = sla.lu_factor(last.A.toarray())
 
     def sizes(self):
         return [lev.n for lev in self.levels]
@@ -214,6 +227,11 @@ class Hierarchy:
         lev = self.levels[l]
         if lev.lu is not None:
             return sla.lu_solve(lev.lu, b)
+        if l == len(self.levels) - 1:          # stalled coarsest level: smoothing only
+            x = np.zeros_like(b)
+            for _ in range(4):
+                x = self.smooth(lev, b, x)
+            return x
         x = np.zeros_like(b)
         for _ in range(self.nu_pre):
             x = self.smooth(lev, b, x)

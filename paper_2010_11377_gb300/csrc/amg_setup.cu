@@ -3,7 +3,9 @@
 // IFISS smoothed aggregation and fixes no further parameter).
 //
 // Per level:
-//   strength   (|a_ij| + |a_ji|)/2 >= theta sqrt(|a_ii a_jj|)   (symmetric graph)
+//   strength   (|a_ij| + |a_ji|)/2 >= theta_l sqrt(|a_ii a_jj|)  (symmetric graph);
+//              theta_l = theta, halved (at most 6 times) while more than a
+//              quarter of the level's nodes have no strong coupling
 //   roots      maximal distance-2 independent set chosen by fixed 64-bit
 //              priorities (fmix32 hash of the index, salted by the level):
 //              in each round an undecided node becomes a root when its key is
@@ -79,7 +81,8 @@ __global__ void k_diag(int n, const int* __restrict__ rp, const int* __restrict_
 // strength flags per entry and strong count per row
 __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ col,
                            const double* __restrict__ val, const double* __restrict__ diag,
-                           double theta, unsigned char* __restrict__ strong, int* __restrict__ cnt) {
+                           double theta, unsigned char* __restrict__ strong, int* __restrict__ cnt,
+                           int* __restrict__ niso) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int c0 = 0;
@@ -97,6 +100,7 @@ __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restr
     c0 += s;
   }
   cnt[r] = c0;
+  if (c0 == 0) atomicAdd(niso, 1);
 }
 
 __global__ void k_strength_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
@@ -386,11 +390,18 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
   std::memcpy(&rho, &rb, sizeof(double));
   double omega = 4.0 / (3.0 * rho);
 
-  // strength graph
+  // strength graph (threshold halved while more than n/4 nodes are isolated)
   unsigned char* strong = tmp.get<unsigned char>(A.nnz > 0 ? A.nnz : 1);
   int* scnt = tmp.get<int>(n + 1);
-  k_strength<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, p.theta, strong, scnt);
-  CK_LAUNCH();
+  int* niso = tmp.get<int>(1);
+  double theta_l = p.theta;
+  for (int halving = 0;; ++halving) {
+    CK(cudaMemsetAsync(niso, 0, sizeof(int), st));
+    k_strength<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, theta_l, strong, scnt, niso);
+    CK_LAUNCH();
+    if (halving == 6 || 4 * int64_t(rd(niso, st)) <= int64_t(n)) break;
+    theta_l *= 0.5;
+  }
   int* grp = tmp.get<int>(n + 1);
   scan_exclusive(scnt, grp, n, st);
   int gnnz = rd(grp + n, st);
@@ -492,12 +503,8 @@ void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaS
     H.lv.push_back(nl);
   }
   Level& last = H.lv.back();
-  if (last.n > MAX_COARSE) {
-    char buf[160];
-    std::snprintf(buf, sizeof(buf), "coarsest AMG level has %d rows (> %d); raise max_levels", last.n,
-                  MAX_COARSE);
-    fail(IRK_ERR_CAPACITY, buf);
-  }
+  // a coarsest level above coarse_max (stalled coarsening) is smoothed, not inverted
+  H.coarse_smooth = last.n > coarse_max;
   // per-level SELL matrices, l1 inverse diagonals, work vectors
   for (size_t l = 0; l < H.lv.size(); ++l) {
     Level& L = H.lv[l];
@@ -515,8 +522,8 @@ void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaS
   }
   // coarsest dense inverse
   int nL = last.n;
-  H.nc_dense = nL;
-  {
+  H.nc_dense = H.coarse_smooth ? 0 : nL;
+  if (!H.coarse_smooth) {
     Tmp tmp;
     double* aug = tmp.get<double>(size_t(nL) * 2 * nL + 1);
     int* bad = tmp.get<int>(1);

@@ -40,6 +40,34 @@ void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 #define CK_LAUNCH() ::irk::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with launch_k may begin
+// while the previous kernel on the stream drains.  Every such kernel calls
+// pdl_wait() before it touches global memory (the wait returns once the
+// previous grid has completed and its writes are visible), and pdl_trigger()
+// to let its own successor launch early.  IRK_PDL=0 disables the attribute.
+// ---------------------------------------------------------------------------
+bool pdl_enabled();
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  CK(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
+// ---------------------------------------------------------------------------
 // Device memory owned by a context (freed at irk_destroy).
 // ---------------------------------------------------------------------------
 struct DevPool {
@@ -156,6 +184,7 @@ struct Hier {
   std::vector<Level> lv;
   void* cinv = nullptr;      // coarsest dense inverse, row-major, V-cycle precision
   int nc_dense = 0;
+  bool coarse_smooth = false;  // stalled coarsest level: 4 smoothing sweeps instead
 };
 
 struct AmgParams {
@@ -328,6 +357,8 @@ void sell_share_pattern(const Sell& pat, const double* csr_vals, const CsrD& A, 
                         int want32, DevPool& pool, cudaStream_t st);
 void csr_transpose(const CsrD& A, CsrD& T, DevPool& pool, cudaStream_t st);
 int choose_lanes(int64_t nnz, int n);
+int autotune_lanes(const CsrD& A, int prec, cudaStream_t st);
+void matT_spmv_launch(const MatT& m, int prec, const void* x, void* y, cudaStream_t st);
 // V-cycle operator in precision prec (64, 32, 16 = BF16) from an FP64 CSR that
 // stays alive (its index arrays are shared); force_lanes > 0 fixes the layout
 void make_matT(const CsrD& A, MatT& m, int prec, DevPool& pool, cudaStream_t st, int force_lanes = 0);

@@ -114,6 +114,8 @@ template <int S, typename TZ, int MODE>
 __global__ void __launch_bounds__(BS)
 k_kron(int n, SellView<double> Mv, const double* __restrict__ Fval, JPtr<const TZ> zp, JPtr<double> wp,
        KronCoef K, const double* __restrict__ bsub, GmresState* st, double* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
   if (st) {
     if (st->done) return;
     if (MODE == 1 && !st->cycle_end) return;
@@ -196,6 +198,8 @@ constexpr int CH = 16;
 template <int PASS>
 __global__ void __launch_bounds__(BS)
 k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, double* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
   if (st->done) return;
   if (PASS == 1 && !st->reorth) return;
   int j = st->j;
@@ -203,14 +207,18 @@ k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, 
   int nvec = (PASS == 0) ? j + 2 : j + 1;   // PASS 0 also takes <w, w>
   for (int i0 = 0; i0 < nvec; i0 += CH) {
     double acc[CH];
-#pragma unroll
-    for (int q = 0; q < CH; ++q) acc[q] = 0.0;
+    const double* __restrict__ vq[CH];
     int cnt = nvec - i0 < CH ? nvec - i0 : CH;
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      acc[q] = 0.0;
+      vq[q] = V + int64_t(i0 + (q < cnt ? q : 0)) * ldv;
+    }
     for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
       double we = w[e];
 #pragma unroll
       for (int q = 0; q < CH; ++q)
-        if (q < cnt) acc[q] = fma(V[int64_t(i0 + q) * ldv + e], we, acc[q]);
+        if (q < cnt) acc[q] = fma(vq[q][e], we, acc[q]);
     }
     block_sum_store<CH>(acc, partials + int64_t(blockIdx.x) * PL + i0, cnt);
   }
@@ -236,6 +244,8 @@ k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, 
 template <int PASS>
 __global__ void __launch_bounds__(BS)
 k_gs_axpy(GmresState* st, double* __restrict__ V, int64_t ldv, int64_t N, double* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
   if (st->done) return;
   if (PASS == 1 && !st->reorth) return;
   __shared__ double coef[MAX_M + 1];
@@ -247,14 +257,9 @@ k_gs_axpy(GmresState* st, double* __restrict__ V, int64_t ldv, int64_t N, double
   double nrm = 0.0;
   for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
     double we = w[e];
-    int i = 0;
-    for (; i + 4 <= j + 1; i += 4) {
-      we = fma(-coef[i], V[int64_t(i) * ldv + e], we);
-      we = fma(-coef[i + 1], V[int64_t(i + 1) * ldv + e], we);
-      we = fma(-coef[i + 2], V[int64_t(i + 2) * ldv + e], we);
-      we = fma(-coef[i + 3], V[int64_t(i + 3) * ldv + e], we);
-    }
-    for (; i <= j; ++i) we = fma(-coef[i], V[int64_t(i) * ldv + e], we);
+    const double* __restrict__ vp = V + e;
+#pragma unroll 4
+    for (int i = 0; i <= j; ++i, vp += ldv) we = fma(-coef[i], *vp, we);
     w[e] = we;
     nrm = fma(we, we, nrm);
   }
@@ -279,6 +284,8 @@ k_gs_axpy(GmresState* st, double* __restrict__ V, int64_t ldv, int64_t N, double
 template <typename TZ>
 __global__ void __launch_bounds__(BS)
 k_xupdate(GmresState* st, const TZ* __restrict__ Z, int64_t ldz, double* __restrict__ x, int64_t N) {
+  pdl_trigger();
+  pdl_wait();
   if (st->done || !st->cycle_end) return;
   __shared__ double y[MAX_M];
   int k = st->j + 1;
@@ -345,6 +352,8 @@ __global__ void __launch_bounds__(BS)
 k_rhs_forward(int n, SellView<double> Fv, const double* __restrict__ u, const double* __restrict__ g,
               double* __restrict__ b, double* __restrict__ V0, double* __restrict__ x, GmresState* st,
               double* __restrict__ partials, int m, int max_it, double rtol, int force) {
+  pdl_trigger();
+  pdl_wait();
   double nrm = 0.0;
   for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
     int sl = r >> 5, lane = r & 31;
@@ -375,6 +384,8 @@ __global__ void __launch_bounds__(BS)
 k_rhs_adjoint(int n, KronCoef hb, const double* __restrict__ lam, double* __restrict__ b,
               double* __restrict__ V0, double* __restrict__ x, GmresState* st, double* __restrict__ partials,
               int m, int max_it, double rtol, int force) {
+  pdl_trigger();
+  pdl_wait();
   double nrm = 0.0;
   for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
     double l = lam[r];
@@ -396,6 +407,8 @@ k_rhs_adjoint(int n, KronCoef hb, const double* __restrict__ lam, double* __rest
 template <int S>
 __global__ void __launch_bounds__(BS)
 k_stage_update(int n, KronCoef hb, const double* __restrict__ k, double* __restrict__ u) {
+  pdl_trigger();
+  pdl_wait();
   for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
     double s = u[r];
 #pragma unroll
@@ -437,6 +450,8 @@ template <int S>
 __global__ void __launch_bounds__(BS)
 k_adj_lambda(int n, SellView<double> Fv, const double* __restrict__ mu, const double* __restrict__ lin,
              double* __restrict__ lout) {
+  pdl_trigger();
+  pdl_wait();
   for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
     int sl = r >> 5, lane = r & 31;
     int64_t base = Fv.sptr[sl];
@@ -550,27 +565,27 @@ int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
   bool z32 = c.amg.amg_prec != 64;
   IRK_DISPATCH_S(c.s, {
     if (z32)
-      k_kron<S, float, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+      launch_k(k_kron<S, float, 0>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64,
                                             JPtr<const float>{static_cast<const float*>(c.Z), jp, N, 0, 0},
                                             JPtr<double>{c.V, jp, N, 1, 0}, K, nullptr, c.st, c.partials);
     else
-      k_kron<S, double, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+      launch_k(k_kron<S, double, 0>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64,
                                              JPtr<const double>{static_cast<const double*>(c.Z), jp, N, 0, 0},
                                              JPtr<double>{c.V, jp, N, 1, 0}, K, nullptr, c.st, c.partials);
   });
   ++launches;
-  k_gs_dots<0><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
-  k_gs_axpy<0><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
-  k_gs_dots<1><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
-  k_gs_axpy<1><<<G, BS, 0, st>>>(c.st, c.V, N, N, c.partials);
+  launch_k(k_gs_dots<0>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
+  launch_k(k_gs_axpy<0>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
+  launch_k(k_gs_dots<1>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
+  launch_k(k_gs_axpy<1>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
   launches += 4;
   if (z32)
-    k_xupdate<float><<<G, BS, 0, st>>>(c.st, static_cast<const float*>(c.Z), N, c.x, N);
+    launch_k(k_xupdate<float>, G, BS, 0, st, c.st, static_cast<const float*>(c.Z), N, c.x, N);
   else
-    k_xupdate<double><<<G, BS, 0, st>>>(c.st, static_cast<const double*>(c.Z), N, c.x, N);
+    launch_k(k_xupdate<double>, G, BS, 0, st, c.st, static_cast<const double*>(c.Z), N, c.x, N);
   ++launches;
   IRK_DISPATCH_S(c.s, {
-    k_kron<S, double, 1><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64, JPtr<const double>{c.x, nullptr, 0, 0, 0},
+    launch_k(k_kron<S, double, 1>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64, JPtr<const double>{c.x, nullptr, 0, 0, 0},
                                            JPtr<double>{c.V, nullptr, 0, 0, 0}, K, c.bv, c.st, c.partials);
   });
   ++launches;
@@ -644,11 +659,11 @@ void profile_kron_launch(Ctx& c, cudaStream_t st) {
   bool z32 = c.amg.amg_prec != 64;
   IRK_DISPATCH_S(c.s, {
     if (z32)
-      k_kron<S, float, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+      launch_k(k_kron<S, float, 0>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64,
                                             JPtr<const float>{static_cast<const float*>(c.Z), nullptr, N, 0, 0},
                                             JPtr<double>{c.V, nullptr, N, 1, 0}, c.K, nullptr, nullptr, nullptr);
     else
-      k_kron<S, double, 0><<<G, BS, 0, st>>>(n, view<double>(c.Ms), c.Fs.v64,
+      launch_k(k_kron<S, double, 0>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64,
                                              JPtr<const double>{static_cast<const double*>(c.Z), nullptr, N, 0, 0},
                                              JPtr<double>{c.V, nullptr, N, 1, 0}, c.K, nullptr, nullptr, nullptr);
   });
@@ -658,8 +673,8 @@ void profile_kron_launch(Ctx& c, cudaStream_t st) {
 // one Gram-Schmidt pass on a scratch state (axpy: also the Givens update)
 void profile_gs_launch(Ctx& c, GmresState* scratch, bool axpy, cudaStream_t st) {
   unsigned G = row_grid(c);
-  if (axpy) k_gs_axpy<0><<<G, BS, 0, st>>>(scratch, c.V, c.N, c.N, c.partials);
-  else k_gs_dots<0><<<G, BS, 0, st>>>(scratch, c.V, c.N, c.N, c.partials);
+  if (axpy) launch_k(k_gs_axpy<0>, G, BS, 0, st, scratch, c.V, c.N, c.N, c.partials);
+  else launch_k(k_gs_dots<0>, G, BS, 0, st, scratch, c.V, c.N, c.N, c.partials);
   CK_LAUNCH();
 }
 
@@ -670,7 +685,7 @@ void set_loop_condition_launch(Ctx& c, cudaGraphConditionalHandle h, cudaStream_
 
 void rhs_forward_launch(Ctx& c, const double* u, cudaStream_t st) {
   IRK_DISPATCH_S(c.s, {
-    k_rhs_forward<S><<<row_grid(c), BS, 0, st>>>(c.n, view<double>(c.Fs), u, c.g, c.bv, c.V, c.x, c.st, c.partials,
+    launch_k(k_rhs_forward<S>, row_grid(c), BS, 0, st, c.n, view<double>(c.Fs), u, c.g, c.bv, c.V, c.x, c.st, c.partials,
                                                  c.m, c.max_it, c.rtol, c.reorth);
   });
   CK_LAUNCH();
@@ -681,7 +696,7 @@ void rhs_adjoint_launch(Ctx& c, const double* lam, cudaStream_t st) {
   for (int i = 0; i < MAX_S * MAX_S; ++i) hb.a[i] = 0.0;
   for (int i = 0; i < c.s; ++i) hb.a[i] = c.h * c.b[i];
   IRK_DISPATCH_S(c.s, {
-    k_rhs_adjoint<S><<<row_grid(c), BS, 0, st>>>(c.n, hb, lam, c.bv, c.V, c.x, c.st, c.partials, c.m, c.max_it,
+    launch_k(k_rhs_adjoint<S>, row_grid(c), BS, 0, st, c.n, hb, lam, c.bv, c.V, c.x, c.st, c.partials, c.m, c.max_it,
                                                  c.rtol, c.reorth);
   });
   CK_LAUNCH();
@@ -691,7 +706,7 @@ void stage_update_launch(Ctx& c, double* u, cudaStream_t st) {
   KronCoef hb;
   for (int i = 0; i < MAX_S * MAX_S; ++i) hb.a[i] = 0.0;
   for (int i = 0; i < c.s; ++i) hb.a[i] = c.h * c.b[i];
-  IRK_DISPATCH_S(c.s, { k_stage_update<S><<<row_grid(c), BS, 0, st>>>(c.n, hb, c.x, u); });
+  IRK_DISPATCH_S(c.s, { launch_k(k_stage_update<S>, row_grid(c), BS, 0, st, c.n, hb, c.x, u); });
   CK_LAUNCH();
 }
 
@@ -703,7 +718,7 @@ void record_launch(Ctx& c, cudaStream_t st) {
 void kron_apply_plain(Ctx& c, const double* z, double* w, bool transpose, cudaStream_t st) {
   const KronCoef& K = transpose ? c.KT : c.K;
   IRK_DISPATCH_S(c.s, {
-    k_kron<S, double, 0><<<row_grid(c), BS, 0, st>>>(c.n, view<double>(c.Ms), c.Fs.v64,
+    launch_k(k_kron<S, double, 0>, row_grid(c), BS, 0, st, c.n, view<double>(c.Ms), c.Fs.v64,
                                                      JPtr<const double>{z, nullptr, 0, 0, 0},
                                                      JPtr<double>{w, nullptr, 0, 0, 0}, K, nullptr, nullptr, nullptr);
   });
@@ -716,7 +731,7 @@ void mass_apply_launch(Ctx& c, const double* x, double* y, cudaStream_t st) {
 }
 
 void adjoint_lambda_launch(Ctx& c, const double* lam_in, double* lam_out, cudaStream_t st) {
-  IRK_DISPATCH_S(c.s, { k_adj_lambda<S><<<row_grid(c), BS, 0, st>>>(c.n, view<double>(c.Fs), c.x, lam_in, lam_out); });
+  IRK_DISPATCH_S(c.s, { launch_k(k_adj_lambda<S>, row_grid(c), BS, 0, st, c.n, view<double>(c.Fs), c.x, lam_in, lam_out); });
   CK_LAUNCH();
 }
 

@@ -7,6 +7,10 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace irk {
 
@@ -49,6 +53,15 @@ void DevPool::free_all() {
 
 Tmp::~Tmp() {
   for (void* p : ptrs) cudaFree(p);
+}
+
+bool pdl_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("IRK_PDL");
+    on = (e && std::atoi(e) == 0) ? 0 : 1;
+  }
+  return on == 1;
 }
 
 int num_sms() {
@@ -331,11 +344,93 @@ int choose_lanes(int64_t nnz, int n) {
   return 32;
 }
 
+// ---------------------------------------------------------------------------
+// Layout autotuner: for an operator of a given shape class (log2 of the rows,
+// log2 of the mean row length, precision) time y = A x with every candidate
+// thread tile (SELL thread-per-row, or CSR with 2..32 lanes per row) and keep
+// the fastest.  Decisions are cached for the process, so repeated set-ups
+// (batches, kappa updates) reuse them.  IRK_AUTOTUNE=0 uses the row-length rule.
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+int ilog2(double v) {
+  int k = 0;
+  while (v >= 2.0) {
+    v *= 0.5;
+    ++k;
+  }
+  return k;
+}
+
+bool autotune_enabled() {
+  const char* e = std::getenv("IRK_AUTOTUNE");
+  return !(e && std::atoi(e) == 0);
+}
+}  // namespace
+
+static void build_layout(const CsrD& A, MatT& m, int prec, int lanes, DevPool& pool, cudaStream_t st);
+
+int autotune_lanes(const CsrD& A, int prec, cudaStream_t st) {
+  int heuristic = choose_lanes(A.nnz, A.n);
+  if (!autotune_enabled() || A.n < 64 || A.nnz == 0) return heuristic;
+  double avg = double(A.nnz) / A.n;
+  auto key = std::make_tuple(ilog2(A.n), ilog2(avg * 2.0), prec);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  const int cand[] = {1, 2, 4, 8, 16, 32};
+  size_t es = prec == 64 ? 8 : 4;
+  DevPool tmp;
+  void* x = tmp.alloc(es * (A.ncols > 0 ? A.ncols : 1));
+  void* y = tmp.alloc(es * A.n);
+  CK(cudaMemsetAsync(x, 0, es * A.ncols, st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = heuristic;
+  float best_t = 1e30f;
+  for (int L : cand) {
+    if (L > 1 && avg < L / 2.0) continue;      // more lanes than half the row: idle lanes
+    if (L == 1 && avg > 48.0) continue;         // one thread walking a long row
+    MatT m;
+    DevPool mp;
+    build_layout(A, m, prec, L, mp, st);
+    for (int w = 0; w < 2; ++w) matT_spmv_launch(m, prec, x, y, st);
+    CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < 5; ++r) matT_spmv_launch(m, prec, x, y, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    if (t < best_t) {
+      best_t = t;
+      best = L;
+    }
+    mp.free_all();
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tmp.free_all();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
 void make_matT(const CsrD& A, MatT& m, int prec, DevPool& pool, cudaStream_t st, int force_lanes) {
+  int lanes = force_lanes > 0 ? force_lanes : autotune_lanes(A, prec == 16 ? 32 : prec, st);
+  build_layout(A, m, prec, lanes, pool, st);
+}
+
+static void build_layout(const CsrD& A, MatT& m, int prec, int lanes, DevPool& pool, cudaStream_t st) {
+  m = MatT{};
   m.n = A.n;
   m.ncols = A.ncols;
   m.nnz = A.nnz;
-  m.lanes = force_lanes > 0 ? force_lanes : choose_lanes(A.nnz, A.n);
+  m.lanes = lanes;
   if (m.lanes == 1) {
     csr_to_sell(A, m.sell, prec == 64, prec == 32, prec == 16, pool, st);
     return;

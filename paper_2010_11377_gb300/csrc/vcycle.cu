@@ -79,6 +79,8 @@ template <typename V, typename T, int L, int XM>
 __global__ void __launch_bounds__(256)
 k_smooth(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ xin,
          const T* din, T* __restrict__ xout, T* dout, T alpha, T beta, T beta0, JPtr<T> out) {
+  pdl_trigger();
+  pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
   int r = gid / L, lane = gid % L;
   bool valid = r < A.n;
@@ -113,6 +115,8 @@ template <typename V, typename T, int L, int XM>
 __global__ void __launch_bounds__(256)
 k_resid(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x, T beta0,
         T* __restrict__ r_out) {
+  pdl_trigger();
+  pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
   int r = gid / L, lane = gid % L;
   bool valid = r < A.n;
@@ -126,6 +130,8 @@ k_resid(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T*
 template <typename T, int L>
 __global__ void __launch_bounds__(256)
 k_spmv(LMat<T> A, const T* __restrict__ x, T* __restrict__ y) {
+  pdl_trigger();
+  pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
   int r = gid / L, lane = gid % L;
   bool valid = r < A.n;
@@ -137,6 +143,8 @@ k_spmv(LMat<T> A, const T* __restrict__ x, T* __restrict__ y) {
 template <typename T, int L, bool IMPLICIT>
 __global__ void __launch_bounds__(256)
 k_prolong(LMat<T> P, const T* __restrict__ e, T* x, const T* __restrict__ dinv, const T* __restrict__ b, T beta0) {
+  pdl_trigger();
+  pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
   int r = gid / L, lane = gid % L;
   bool valid = r < P.n;
@@ -148,6 +156,8 @@ k_prolong(LMat<T> P, const T* __restrict__ e, T* x, const T* __restrict__ dinv, 
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, JPtr<T> out) {
+  pdl_trigger();
+  pdl_wait();
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -163,6 +173,8 @@ k_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __rest
 
 template <typename T>
 __global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
+  pdl_trigger();
+  pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) out.get()[r] = src[r];
 }
@@ -171,6 +183,7 @@ __global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
 #define IRK_DISPATCH_L(LANES, ...)                          \
   switch (LANES) {                                          \
     case 1: { constexpr int LN = 1; __VA_ARGS__; } break;    \
+    case 2: { constexpr int LN = 2; __VA_ARGS__; } break;    \
     case 4: { constexpr int LN = 4; __VA_ARGS__; } break;    \
     case 8: { constexpr int LN = 8; __VA_ARGS__; } break;    \
     case 16: { constexpr int LN = 16; __VA_ARGS__; } break;  \
@@ -179,6 +192,21 @@ __global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
   }
 
 static inline unsigned grid_for(const MatT& m) { return nblk(int64_t(m.n) * m.lanes); }
+
+// y = m x in the V-cycle precision (prec 64: FP64, else FP32 vectors); used by
+// the layout autotuner
+void matT_spmv_launch(const MatT& m, int prec, const void* x, void* y, cudaStream_t st) {
+  if (prec == 64) {
+    LMat<double> A = lmat<double>(m);
+    IRK_DISPATCH_L(m.lanes, { launch_k(k_spmv<double, LN>, grid_for(m), 256, 0, st, A, static_cast<const double*>(x),
+                                                                               static_cast<double*>(y)); });
+  } else {
+    LMat<float> A = lmat<float>(m);
+    IRK_DISPATCH_L(m.lanes, { launch_k(k_spmv<float, LN>, grid_for(m), 256, 0, st, A, static_cast<const float*>(x),
+                                                                              static_cast<float*>(y)); });
+  }
+  CK_LAUNCH();
+}
 
 // ---------------------------------------------------------------------------
 // V-cycle driver (kernel sequence; captured into CUDA graphs by the caller)
@@ -207,7 +235,7 @@ struct VCycle {
   void smooth(const Level& L, const T* xin, const T* din, T* xout, T* dout, int step, JPtr<T> out) {
     LMat<V> A = lmat<V>(L.Am);
     IRK_DISPATCH_L(L.Am.lanes, {
-      k_smooth<V, T, LN, XM><<<grid_for(L.Am), 256, 0, st>>>(A, static_cast<const T*>(L.dinv),
+      launch_k(k_smooth<V, T, LN, XM>, grid_for(L.Am), 256, 0, st, A, static_cast<const T*>(L.dinv),
                                                            static_cast<const T*>(L.b), xin, din, xout, dout,
                                                            T(sc.alpha[step]), T(sc.beta[step]), T(sc.beta[0]), out);
     });
@@ -227,10 +255,42 @@ struct VCycle {
     T* rb = static_cast<T*>(L.r);
     JPtr<T> none = jptr<T>(nullptr);
     int last = static_cast<int>(H.lv.size()) - 1;
+    if (l == last && H.coarse_smooth) {
+      // stalled coarsest level: 4 smoothing sweeps from zero
+      const int steps = sc.steps;
+      bool implicit = false;
+      T* cur = xb;
+      T* oth = yb;
+      int total = 4 * steps, q = 0;
+      for (int sw = 0; sw < 4; ++sw) {
+        for (int k = 0; k < steps; ++k, ++q) {
+          bool final_step = (q == total - 1);
+          JPtr<T> o = (final_step && out.base) ? out : none;
+          if (sw == 0 && k == 0) {
+            if (total == 1) {
+              smooth<V, XM_ZERO>(L, nullptr, nullptr, cur, db, 0, o);
+              break;
+            }
+            implicit = true;
+            continue;
+          }
+          if (implicit) {
+            smooth<V, XM_IMPLICIT>(L, nullptr, nullptr, cur, db, k, o);
+            implicit = false;
+          } else {
+            smooth<V, XM_EXPLICIT>(L, cur, k == 0 ? nullptr : db, oth, db, k, o);
+            T* t = cur;
+            cur = oth;
+            oth = t;
+          }
+        }
+      }
+      return out.base ? nullptr : cur;
+    }
     if (l == last) {
       int nl = L.n;
       unsigned blocks = nblk(int64_t(nl) * 32);
-      k_dense_mv<T><<<blocks, 256, 0, st>>>(nl, static_cast<const T*>(H.cinv), b, xb, out);
+      launch_k(k_dense_mv<T>, blocks, 256, 0, st, nl, static_cast<const T*>(H.cinv), b, xb, out);
       ++launches;
       cost.bytes += double(nl) * nl * sizeof(T) + 2.0 * nl * sizeof(T);
       cost.flops += 2.0 * double(nl) * nl;
@@ -265,9 +325,9 @@ struct VCycle {
       const T* dv = static_cast<const T*>(L.dinv);
       IRK_DISPATCH_L(L.Am.lanes, {
         if (implicit)
-          k_resid<V, T, LN, XM_IMPLICIT><<<grid_for(L.Am), 256, 0, st>>>(A, dv, b, nullptr, beta0, rb);
+          launch_k(k_resid<V, T, LN, XM_IMPLICIT>, grid_for(L.Am), 256, 0, st, A, dv, b, nullptr, beta0, rb);
         else
-          k_resid<V, T, LN, XM_EXPLICIT><<<grid_for(L.Am), 256, 0, st>>>(A, dv, b, cur, beta0, rb);
+          launch_k(k_resid<V, T, LN, XM_EXPLICIT>, grid_for(L.Am), 256, 0, st, A, dv, b, cur, beta0, rb);
       });
       ++launches;
       count_matvec<V>(L, 2, 1);
@@ -276,7 +336,7 @@ struct VCycle {
     {
       LMat<T> R = lmat<T>(L.Rm);
       const T* src = p.nu_pre > 0 ? rb : b;
-      IRK_DISPATCH_L(L.Rm.lanes, { k_spmv<T, LN><<<grid_for(L.Rm), 256, 0, st>>>(R, src, static_cast<T*>(C.b)); });
+      IRK_DISPATCH_L(L.Rm.lanes, { launch_k(k_spmv<T, LN>, grid_for(L.Rm), 256, 0, st, R, src, static_cast<T*>(C.b)); });
     }
     ++launches;
     cost.bytes += double(L.Rm.nnz) * (sizeof(int) + sizeof(T)) + double(L.n + C.n) * sizeof(T);
@@ -289,9 +349,9 @@ struct VCycle {
       if (p.nu_pre == 0) CK(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, st));
       IRK_DISPATCH_L(L.Pm.lanes, {
         if (p.nu_pre > 0 && implicit)
-          k_prolong<T, LN, true><<<grid_for(L.Pm), 256, 0, st>>>(P, e, cur, dv, b, beta0);
+          launch_k(k_prolong<T, LN, true>, grid_for(L.Pm), 256, 0, st, P, e, cur, dv, b, beta0);
         else
-          k_prolong<T, LN, false><<<grid_for(L.Pm), 256, 0, st>>>(P, e, cur, nullptr, nullptr, beta0);
+          launch_k(k_prolong<T, LN, false>, grid_for(L.Pm), 256, 0, st, P, e, cur, nullptr, nullptr, beta0);
       });
     }
     ++launches;
@@ -311,7 +371,7 @@ struct VCycle {
       }
     }
     if (total == 0 && out.base) {
-      k_copy_out<T><<<nblk(L.n), 256, 0, st>>>(L.n, cur, out);
+      launch_k(k_copy_out<T>, nblk(L.n), 256, 0, st, L.n, cur, out);
       ++launches;
     }
     return out.base ? nullptr : cur;
@@ -387,6 +447,8 @@ __global__ void __launch_bounds__(256)
 k_sweep_rhs(SellView<T> F, const double* __restrict__ V, const int* __restrict__ jp, int64_t ldv,
             int64_t voff, const double* __restrict__ sigma, const T* __restrict__ Z, int64_t ldz,
             Couplings cp, const int* __restrict__ skip, T* __restrict__ out) {
+  pdl_trigger();
+  pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int n = F.n;
   if (r >= n) return;
@@ -431,7 +493,7 @@ static void launch_sweep_rhs(int np, SellView<T> F, const double* V, const int* 
   unsigned g = nblk(F.n);
   switch (np) {
 #define IRK_SW(NPV) \
-  case NPV: k_sweep_rhs<T, NPV><<<g, 256, 0, st>>>(F, V, jp, ldv, voff, sigma, Z, ldz, cp, skip, out); break;
+  case NPV: launch_k(k_sweep_rhs<T, NPV>, g, 256, 0, st, F, V, jp, ldv, voff, sigma, Z, ldz, cp, skip, out); break;
     IRK_SW(0) IRK_SW(1) IRK_SW(2) IRK_SW(3) IRK_SW(4) IRK_SW(5) IRK_SW(6) IRK_SW(7)
 #undef IRK_SW
     default: fail(IRK_ERR_INVALID, "too many stage couplings");
