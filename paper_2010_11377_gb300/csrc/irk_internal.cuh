@@ -43,13 +43,15 @@ void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 // Programmatic dependent launch: a kernel launched with launch_k may begin
 // while the previous kernel on the stream drains.  Every such kernel calls
 // pdl_wait() before it touches global memory (the wait returns once the
-// previous grid has completed and its writes are visible), and pdl_trigger()
-// to let its own successor launch early.  IRK_PDL=0 disables the attribute.
+// previous grid has completed and its writes are visible).  IRK_PDL=0
+// disables the attribute.
 // ---------------------------------------------------------------------------
 bool pdl_enabled();
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+// dependents launch when this grid's blocks exit (no early trigger: measured,
+// an early trigger let waiting blocks crowd the tail of multi-wave grids)
+__device__ __forceinline__ void pdl_trigger() {}
 
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

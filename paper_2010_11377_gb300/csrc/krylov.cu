@@ -207,18 +207,14 @@ k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, 
   int nvec = (PASS == 0) ? j + 2 : j + 1;   // PASS 0 also takes <w, w>
   for (int i0 = 0; i0 < nvec; i0 += CH) {
     double acc[CH];
-    const double* __restrict__ vq[CH];
-    int cnt = nvec - i0 < CH ? nvec - i0 : CH;
 #pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      acc[q] = 0.0;
-      vq[q] = V + int64_t(i0 + (q < cnt ? q : 0)) * ldv;
-    }
+    for (int q = 0; q < CH; ++q) acc[q] = 0.0;
+    int cnt = nvec - i0 < CH ? nvec - i0 : CH;
     for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
       double we = w[e];
 #pragma unroll
       for (int q = 0; q < CH; ++q)
-        if (q < cnt) acc[q] = fma(vq[q][e], we, acc[q]);
+        if (q < cnt) acc[q] = fma(V[int64_t(i0 + q) * ldv + e], we, acc[q]);
     }
     block_sum_store<CH>(acc, partials + int64_t(blockIdx.x) * PL + i0, cnt);
   }
@@ -257,9 +253,14 @@ k_gs_axpy(GmresState* st, double* __restrict__ V, int64_t ldv, int64_t N, double
   double nrm = 0.0;
   for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
     double we = w[e];
-    const double* __restrict__ vp = V + e;
-#pragma unroll 4
-    for (int i = 0; i <= j; ++i, vp += ldv) we = fma(-coef[i], *vp, we);
+    int i = 0;
+    for (; i + 4 <= j + 1; i += 4) {
+      we = fma(-coef[i], V[int64_t(i) * ldv + e], we);
+      we = fma(-coef[i + 1], V[int64_t(i + 1) * ldv + e], we);
+      we = fma(-coef[i + 2], V[int64_t(i + 2) * ldv + e], we);
+      we = fma(-coef[i + 3], V[int64_t(i + 3) * ldv + e], we);
+    }
+    for (; i <= j; ++i) we = fma(-coef[i], V[int64_t(i) * ldv + e], we);
     w[e] = we;
     nrm = fma(we, we, nrm);
   }
