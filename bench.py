@@ -271,6 +271,20 @@ def cpu_baseline(name, iterations_per_step, budget_s=20.0):
             "seconds_per_iteration": per_it}
 
 
+def aggregate_ranks(ms, units, dist=None, device=None):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of
+    the units every rank processed (replicas, no data-path collective)."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms, float(units)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0].item()), float(sm[1].item())
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -297,11 +311,8 @@ def run_ours(args):
     dev_index = torch.cuda.current_device()
     with ClockSampler(dev_index) as clk:
         ms, st, launches, uN = timed_steps(ctx, u, args.steps, args.warmup, dist)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * s * n * args.steps / (ms * 1e-3)
+    ms, units = aggregate_ranks(ms, s * n * args.steps, dist, device="cuda")
+    value = units / (ms * 1e-3)
     its = st["iterations"] / max(st["steps"], 1)
     if rank != 0:
         if dist:
@@ -349,6 +360,68 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched uneven instances: 64 heat problems on grids 64^2..512^2 (N_i =
+    32 round(2 8^(i/63))), per-element log-diffusion from a Gaussian random
+    field (sigma 0.5, correlation length 0.1), random smooth u0, Radau IIA
+    s = 3, h_t = 1/32, 32 steps, checkpoints every 8; one graph launch runs
+    every instance forward, one more runs the checkpointed adjoint (gradients
+    of 1/2 (u_N - d)^T M (u_N - d) w.r.t. u0 and kappa)."""
+    import numpy as np
+    import torch
+    import synth
+    from __graft_entry__ import build
+    build()
+    from paper_2010_11377_gb300 import binding as B
+    from paper_2010_11377_gb300 import problems
+    s, h, nsteps, every = 3, 1.0 / 32, 32, 8
+    sizes = synth.batch_instance_sizes(args.batch_count)
+    A, b, c = B.irk_butcher_table("radau_iia", s)
+    ctxs, u0s, uNs, cks, lams, grads = [], [], [], [], [], []
+    t0 = time.perf_counter()
+    total_su = 0
+    for i, N in enumerate(sizes):
+        mesh = synth.structured_mesh(N)
+        kap = np.exp(synth.grf_log_kappa(mesh, seed=i))
+        p = problems.heat(N, kappa=kap)
+        ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, mesh=p["mesh_arrays"])
+        ctxs.append(ctx)
+        u0s.append(torch.tensor(synth.random_smooth_u0(mesh, seed=i), dtype=torch.float64, device="cuda"))
+        uNs.append(torch.empty(mesh.n, dtype=torch.float64, device="cuda"))
+        cks.append(torch.empty(nsteps // every, mesh.n, dtype=torch.float64, device="cuda"))
+        lams.append(torch.empty(mesh.n, dtype=torch.float64, device="cuda"))
+        grads.append(torch.zeros(mesh.n_tri, dtype=torch.float64, device="cuda"))
+        total_su += s * mesh.n * nsteps
+    setup_s = time.perf_counter() - t0
+    batch = B.irk_batch_create(ctxs, nsteps, every, u0s, uNs, cks, lams, grads)
+    B.irk_batch_run(batch)                    # warm
+    fwd_ms = []
+    adj_ms = []
+    for _ in range(max(1, args.steps // 4)):
+        st, ms = B.irk_batch_run(batch)
+        fwd_ms.append(ms)
+        for q, ctx in enumerate(ctxs):
+            B.irk_apply_mass(ctx, (uNs[q] - 0.5 * u0s[q]).contiguous(), lams[q])
+            grads[q].zero_()
+        ast, ams = B.irk_batch_adjoint(batch)
+        adj_ms.append(ams)
+    f = min(fwd_ms)
+    a = min(adj_ms)
+    its = sum(x["iterations"] for x in st) / len(st)
+    out = {"metric": METRIC, "value": total_su / (f * 1e-3), "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "config": {"workload": f"batch{len(sizes)}_heat{sizes[0]}-{sizes[-1]}_radau3_LD_f32amg",
+                      "instances": len(sizes), "steps": nsteps, "ckpt_every": every},
+           "forward_ms": f, "adjoint_ms": a, "adjoint_over_forward": a / f,
+           "mean_iterations_per_instance_run": its, "setup_s": setup_s,
+           "launches": {"forward": 1, "adjoint": 1},
+           "grad_norms": {"u0": float(sum(float(l.norm()) ** 2 for l in lams) ** 0.5),
+                          "kappa": float(sum(float(g.norm()) ** 2 for g in grads) ** 0.5)}}
+    print(json.dumps(out))
+    batch.close()
+    for ctx in ctxs:
+        ctx.close()
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle (the paper has no code) on the host cores,
     same metric and workload.  Set-up and one full step (to count its FGMRES
@@ -386,6 +459,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="the batched uneven-instance workload")
+    ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--launch-list", action="store_true",
                     help="only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()
@@ -393,6 +468,8 @@ def main():
         args.no_cpu_baseline = args.no_fp64 = True
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch:
+        run_batch(args)
     else:
         run_ours(args)
 
