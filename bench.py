@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # name: (grid N, stages s, h_t, preconditioner, AMG precision)
     "heat1024_radau5_LD_f32amg": (1024, 5, 1.0 / 64, "LD", "f32"),
+    "heat512_radau5_LD_f32amg": (512, 5, 1.0 / 64, "LD", "f32"),
     "heat256_radau5_LD_f32amg": (256, 5, 1.0 / 64, "LD", "f32"),
     "heat32_radau2_LD_f32amg": (32, 2, 0.05, "LD", "f32"),
 }
@@ -360,6 +361,21 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel(args):
+    """One hot kernel in isolation (irk_profile) on a workload's context: a
+    small, bounded launch sequence for ncu captures.  Prints one JSON line."""
+    from __graft_entry__ import build
+    build()
+    from paper_2010_11377_gb300 import binding as B
+    ctx, prob, _ = build_context(args.workload)
+    res = {}
+    for k in args.kernel.split(","):
+        res[k] = B.irk_profile(ctx, k, j=args.kernel_j, warm=args.kernel_warm, reps=args.kernel_reps)
+    print(json.dumps({"workload": args.workload, "j": args.kernel_j, "warm": args.kernel_warm,
+                      "reps": args.kernel_reps, "kernels": res}))
+    ctx.close()
+
+
 def run_batch(args):
     """Batched uneven instances: 64 heat problems on grids 64^2..512^2 (N_i =
     32 round(2 8^(i/63))), per-element log-diffusion from a Gaussian random
@@ -461,6 +477,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--batch", action="store_true", help="the batched uneven-instance workload")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--kernel", default=None,
+                    help="comma list of kron,vcycle,precond,gs_dots,gs_axpy,smooth0: time these alone")
+    ap.add_argument("--kernel-j", type=int, default=22, help="Gram-Schmidt basis index for --kernel")
+    ap.add_argument("--kernel-warm", type=int, default=3)
+    ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--launch-list", action="store_true",
                     help="only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()
@@ -470,6 +491,8 @@ def main():
         run_reference(args)
     elif args.batch:
         run_batch(args)
+    elif args.kernel:
+        run_kernel(args)
     else:
         run_ours(args)
 

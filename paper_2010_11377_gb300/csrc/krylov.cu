@@ -21,6 +21,65 @@ constexpr int BS = 256;         // threads per block of the outer kernels
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
+// Exact FP32 -> FP64 widening by IEEE-754 field arithmetic on the integer
+// pipe (the conversion instruction shares the narrow FP64 pipe with the
+// DFMAs of the operator).  Normal numbers: sign kept, exponent re-biased by
+// 1023 - 127 = 896, the 23 fraction bits become the top of the 52.  Zero,
+// subnormal, infinite and NaN inputs take the conversion instruction.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) {
+  unsigned u = __float_as_uint(x);
+  unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return static_cast<double>(x);
+  unsigned m = u & 0x7fffffu;
+  unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(m << 29));
+}
+
+// Sum C <= 16 per-thread values over the block; thread t < C writes slot t.
+// Within a warp a transposing butterfly: at each of the first log2(P) xor
+// steps (P = C rounded up to a power of two) a lane keeps one half of its
+// values and adds the partner's copy of that half, so a lane performs P - 1
+// adds (plus 5 - log2 P for the lanes that share an index) instead of 5 C.
+// Lane l then holds value index (l >> (5 - log2 P)) & (P - 1).  The warps'
+// results are added in warp order (deterministic).
+template <int C>
+__device__ __forceinline__ void block_sum_store_t(const double (&v)[C], double* __restrict__ out) {
+  static_assert(C >= 1 && C <= 16, "1..16 values");
+  constexpr int LP = C <= 1 ? 0 : C <= 2 ? 1 : C <= 4 ? 2 : C <= 8 ? 3 : 4;
+  constexpr int P = 1 << LP;
+  __shared__ double sm[BS / 32][P];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double a[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) a[q] = q < C ? v[q] : 0.0;
+#pragma unroll
+  for (int k = 0; k < LP; ++k) {
+    const int half = P >> (k + 1);
+    const int mbit = 16 >> k;
+    const bool up = (lane & mbit) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      double send = up ? a[i] : a[i + half];
+      double keep = up ? a[i + half] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, mbit);
+    }
+  }
+  double x = a[0];
+#pragma unroll
+  for (int mbit = 16 >> LP; mbit > 0; mbit >>= 1) x += __shfl_xor_sync(0xffffffffu, x, mbit);
+  constexpr int SH = 5 - LP;
+  if ((lane & ((1 << SH) - 1)) == 0) sm[warp][(lane >> SH) & (P - 1)] = x;
+  __syncthreads();
+  if (threadIdx.x < C) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < BS / 32; ++w) s += sm[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
 // sum NV per-thread values over the block; thread t < NV writes slot t
 template <int NV>
 __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* __restrict__ out, int cnt = NV) {
@@ -140,7 +199,7 @@ k_kron(int n, SellView<double> Mv, const double* __restrict__ Fval, JPtr<const T
       double f = Fval[idx];
 #pragma unroll
       for (int i = 0; i < S; ++i) {
-        double zz = static_cast<double>(z[int64_t(i) * n + c]);
+        double zz = to_f64(z[int64_t(i) * n + c]);
         mz[i] = fma(m, zz, mz[i]);
         fz[i] = fma(f, zz, fz[i]);
       }
@@ -195,8 +254,25 @@ k_kron(int n, SellView<double> Mv, const double* __restrict__ Fval, JPtr<const T
 // ---------------------------------------------------------------------------
 constexpr int CH = 16;
 
+// C basis vectors starting at i0 against w: per-block partial sums into slots
+// i0 .. i0 + C - 1 (exact count, so no predicated-off DFMAs)
+template <int C>
+__device__ __forceinline__ void dots_chunk(const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+                                           int64_t N, int i0, double* __restrict__ out) {
+  double acc[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) acc[q] = 0.0;
+  const double* __restrict__ Vb = V + int64_t(i0) * ldv;
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
+    double we = w[e];
+#pragma unroll
+    for (int q = 0; q < C; ++q) acc[q] = fma(Vb[int64_t(q) * ldv + e], we, acc[q]);
+  }
+  block_sum_store_t<C>(acc, out + i0);
+}
+
 template <int PASS>
-__global__ void __launch_bounds__(BS)
+__global__ void __launch_bounds__(BS, 4)
 k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, double* __restrict__ partials) {
   pdl_trigger();
   pdl_wait();
@@ -205,18 +281,20 @@ k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, 
   int j = st->j;
   const double* __restrict__ w = V + int64_t(j + 1) * ldv;
   int nvec = (PASS == 0) ? j + 2 : j + 1;   // PASS 0 also takes <w, w>
-  for (int i0 = 0; i0 < nvec; i0 += CH) {
-    double acc[CH];
-#pragma unroll
-    for (int q = 0; q < CH; ++q) acc[q] = 0.0;
-    int cnt = nvec - i0 < CH ? nvec - i0 : CH;
-    for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
-      double we = w[e];
-#pragma unroll
-      for (int q = 0; q < CH; ++q)
-        if (q < cnt) acc[q] = fma(V[int64_t(i0 + q) * ldv + e], we, acc[q]);
+  // near-equal chunks of at most CH vectors
+  int nch = (nvec + CH - 1) / CH;
+  int base = nvec / nch, extra = nvec % nch;
+  double* pb = partials + int64_t(blockIdx.x) * PL;
+  for (int ch = 0, i0 = 0; ch < nch; ++ch) {
+    int cnt = base + (ch < extra ? 1 : 0);
+    switch (cnt) {
+#define IRK_DC(K) case K: dots_chunk<K>(V, ldv, w, N, i0, pb); break;
+      IRK_DC(1) IRK_DC(2) IRK_DC(3) IRK_DC(4) IRK_DC(5) IRK_DC(6) IRK_DC(7) IRK_DC(8)
+      IRK_DC(9) IRK_DC(10) IRK_DC(11) IRK_DC(12) IRK_DC(13) IRK_DC(14) IRK_DC(15) IRK_DC(16)
+#undef IRK_DC
+      default: break;
     }
-    block_sum_store<CH>(acc, partials + int64_t(blockIdx.x) * PL + i0, cnt);
+    i0 += cnt;
   }
   if (last_block(st)) {
     for (int i = threadIdx.x; i < nvec; i += BS) {
@@ -300,7 +378,7 @@ k_xupdate(GmresState* st, const TZ* __restrict__ Z, int64_t ldz, double* __restr
   __syncthreads();
   for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
     double xe = x[e];
-    for (int i = 0; i < k; ++i) xe = fma(y[i], static_cast<double>(Z[int64_t(i) * ldz + e]), xe);
+    for (int i = 0; i < k; ++i) xe = fma(y[i], to_f64(Z[int64_t(i) * ldz + e]), xe);
     x[e] = xe;
   }
 }
