@@ -132,9 +132,16 @@ def timed_steps(ctx, u, steps, warmup, dist=None):
     l0 = B.irk_kernel_launches(ctx)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    try:   # an NVTX range around the timed steps (ncu --nvtx-include "timed_steps/")
+        nvtx.range_push("timed_steps")
+    except Exception:
+        nvtx = None
     e0.record()
     st = B.irk_run(ctx, u, steps, out)
     e1.record()
+    if nvtx:
+        nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

@@ -113,6 +113,10 @@ struct Sell {               // SELL-32
   int64_t nnz_pad = 0;
   int64_t* sptr = nullptr;  // nslices + 1, element offsets
   int* col = nullptr;       // nnz_pad (padding: column 0, value 0)
+  // square matrices whose columns all lie within +-32767 of their row: the
+  // same columns as 16-bit offsets from the row (padding: offset 0), read by
+  // the bandwidth-bound kernels instead of col (2 bytes per entry less)
+  short* dcol = nullptr;
   double* v64 = nullptr;
   float* v32 = nullptr;
   __nv_bfloat16* v16 = nullptr;
@@ -124,7 +128,14 @@ struct SellView {
   const int64_t* __restrict__ sptr;
   const int* __restrict__ col;
   const V* __restrict__ val;
+  const short* __restrict__ dcol;
 };
+
+// column of SELL entry idx of row r
+__device__ __forceinline__ int sell_col(const int* __restrict__ col, const short* __restrict__ dcol, int64_t idx,
+                                        int r) {
+  return dcol ? r + static_cast<int>(dcol[idx]) : col[idx];
+}
 
 template <typename V> const V* sell_vals(const Sell& s);
 template <> inline const double* sell_vals<double>(const Sell& s) { return s.v64; }
@@ -133,11 +144,11 @@ template <> inline const __nv_bfloat16* sell_vals<__nv_bfloat16>(const Sell& s) 
 
 template <typename V>
 inline SellView<V> view(const Sell& s) {
-  return SellView<V>{s.n, s.sptr, s.col, sell_vals<V>(s)};
+  return SellView<V>{s.n, s.sptr, s.col, sell_vals<V>(s), s.dcol};
 }
 
 // One operator of a V-cycle level in the V-cycle precision.  Short rows
-// (mean <= 12 entries): SELL-32, one thread per row.  Longer rows: CSR with
+// (mean <= 16 entries): SELL-32, one thread per row.  Longer rows: CSR with
 // `lanes` threads per row (4..32) and a shuffle reduction, so a coarse
 // Galerkin row of a few hundred entries is not walked by a single thread.
 struct MatT {
@@ -158,12 +169,13 @@ struct LMat {
   const int* __restrict__ rowptr;
   const int* __restrict__ col;
   const V* __restrict__ val;
+  const short* __restrict__ dcol;   // SELL 16-bit column offsets, or null
 };
 
 template <typename V>
 inline LMat<V> lmat(const MatT& m) {
-  if (m.lanes == 1) return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell)};
-  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val)};
+  if (m.lanes == 1) return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell), m.sell.dcol};
+  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), nullptr};
 }
 
 // ---------------------------------------------------------------------------

@@ -194,7 +194,7 @@ k_kron(int n, SellView<double> Mv, const double* __restrict__ Fval, JPtr<const T
     int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
     for (int k = 0; k < wdt; ++k) {
       int64_t idx = base + (int64_t(k) << 5) + lane;
-      int c = Mv.col[idx];
+      int c = sell_col(Mv.col, Mv.dcol, idx, r);
       double m = Mv.val[idx];
       double f = Fval[idx];
 #pragma unroll
@@ -691,7 +691,7 @@ k_resid_partials(int n, SellView<double> Mv, const double* __restrict__ Fval, co
     int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
     for (int q = 0; q < wdt; ++q) {
       int64_t idx = base + (int64_t(q) << 5) + lane;
-      int c = Mv.col[idx];
+      int c = sell_col(Mv.col, Mv.dcol, idx, r);
       double m = Mv.val[idx];
       double f = Fval[idx];
 #pragma unroll

@@ -57,9 +57,16 @@ __device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
       int sl = r >> 5, ln = r & 31;
       int64_t base = A.sptr[sl];
       int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-      for (int k = 0; k < w; ++k) {
-        int64_t idx = base + (int64_t(k) << 5) + ln;
-        acc = fma(widen(A.val[idx]), xf(A.col[idx]), acc);
+      if (A.dcol) {
+        for (int k = 0; k < w; ++k) {
+          int64_t idx = base + (int64_t(k) << 5) + ln;
+          acc = fma(widen(A.val[idx]), xf(r + static_cast<int>(A.dcol[idx])), acc);
+        }
+      } else {
+        for (int k = 0; k < w; ++k) {
+          int64_t idx = base + (int64_t(k) << 5) + ln;
+          acc = fma(widen(A.val[idx]), xf(A.col[idx]), acc);
+        }
       }
     }
   } else {
@@ -227,7 +234,8 @@ struct VCycle {
 
   template <typename V>
   void count_matvec(const Level& L, int vec_reads, int vec_writes) {
-    cost.bytes += double(L.nnz) * (sizeof(int) + sizeof(V)) + double(L.n) * sizeof(T) * (vec_reads + vec_writes);
+    const double idx_bytes = (L.Am.lanes == 1 && L.Am.sell.dcol) ? 2.0 : 4.0;   // 16-bit SELL offsets
+    cost.bytes += double(L.nnz) * (idx_bytes + sizeof(V)) + double(L.n) * sizeof(T) * (vec_reads + vec_writes);
     cost.flops += 2.0 * double(L.nnz) + 4.0 * L.n;
   }
 
@@ -472,7 +480,7 @@ k_sweep_rhs(SellView<T> F, const double* __restrict__ V, const int* __restrict__
   int w = static_cast<int>((F.sptr[sl + 1] - base) >> 5);
   for (int k = 0; k < w; ++k) {
     int64_t idx = base + (int64_t(k) << 5) + lane;
-    int c = F.col[idx];
+    int c = sell_col(F.col, F.dcol, idx, r);
     T f = F.val[idx];
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc[q] = fma(f, zj[int64_t(cp.idx[q]) * n + c], acc[q]);
