@@ -97,8 +97,11 @@ typedef struct {
   int32_t restart;       /* FGMRES restart length m (1..64) */
   double rtol;           /* stop when ||b - A k||_2 <= rtol ||b||_2 */
   int32_t max_it;        /* total inner iterations per solve */
-  int32_t reorth;        /* 0: classical Gram-Schmidt, reorthogonalised when the norm drops
-                            below 1/sqrt(2) of its value; 1: always twice */
+  int32_t reorth;        /* 0: classical Gram-Schmidt with a second pass when the projected
+                            norm drops below reorth_eta of its value; 1: always twice */
+  double reorth_eta;     /* 0 <= reorth_eta < 1; 0: never a second pass.  Default 0.1: one
+                            classical pass loses at most about eps/reorth_eta of orthogonality
+                            per vector, so a second pass is taken only on heavy cancellation */
 } irk_options;
 
 typedef struct {
@@ -136,7 +139,7 @@ irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, 
 
 /* Fill *opt with the defaults: P_LD, FP32 AMG, Chebyshev degree 4 on [0.1, 1],
  * V(1,1), theta 0.08, coarse_max 1024, 12 levels, FGMRES(30), rtol 1e-10,
- * max_it 1000, selective reorthogonalisation. */
+ * max_it 1000, selective reorthogonalisation (reorth_eta 0.1). */
 void irk_default_options(irk_options* opt);
 
 /* ------------------------------------------------------------------------- *

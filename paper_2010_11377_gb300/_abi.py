@@ -26,7 +26,8 @@ class IrkOptions(C.Structure):
                 ("smoother", C.c_int32), ("cheb_degree", C.c_int32), ("cheb_lo", C.c_double),
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("theta", C.c_double),
                 ("coarse_max", C.c_int32), ("max_levels", C.c_int32), ("restart", C.c_int32),
-                ("rtol", C.c_double), ("max_it", C.c_int32), ("reorth", C.c_int32)]
+                ("rtol", C.c_double), ("max_it", C.c_int32), ("reorth", C.c_int32),
+                ("reorth_eta", C.c_double)]
 
 
 class IrkStats(C.Structure):

@@ -383,6 +383,7 @@ void irk_default_options(irk_options* o) {
   o->rtol = 1e-10;
   o->max_it = 1000;
   o->reorth = 0;
+  o->reorth_eta = 0.1;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -419,6 +420,8 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post == 0)
     return set_err(nullptr, IRK_ERR_INVALID, "need at least one smoothing sweep");
   if (!(o.rtol > 0.0) || o.max_it < 1) return set_err(nullptr, IRK_ERR_INVALID, "bad rtol/max_it");
+  if (!(o.reorth_eta >= 0.0 && o.reorth_eta < 1.0) || o.reorth < 0 || o.reorth > 1)
+    return set_err(nullptr, IRK_ERR_INVALID, "reorth must be 0 or 1 and 0 <= reorth_eta < 1");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
     return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..1024");
   const irk_csr& M = prob->M;
@@ -451,6 +454,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     c.max_it = o.max_it;
     c.rtol = o.rtol;
     c.reorth = o.reorth;
+    c.reorth_eta = o.reorth_eta;
     c.kind = o.kind;
     c.amg.theta = o.theta;
     c.amg.coarse_max = o.coarse_max;

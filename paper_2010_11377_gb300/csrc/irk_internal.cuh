@@ -231,11 +231,12 @@ struct GmresState {
   int cycle_end;   // 1: update x and restart or stop after this iteration
   int reorth;      // 1: reorthogonalise this iteration
   int status;      // irk_status from the device
-  int m, max_it, force_reorth;
+  int m, max_it;
   unsigned int counter;   // last-block-done ticket
   int guard;              // loop-body executions of this solve (bounded)
   double bnorm, rtol;
   double wnorm2;          // ||w||^2 before projection
+  double eta2;            // second pass when ||w_proj||^2 < eta2 ||w||^2 (< 0: always)
   double resid;           // last true relative residual
   double H[MAX_M * (MAX_M + 1)];   // column-major, column j at H[j*(MAX_M+1)]
   double cs[MAX_M], sn[MAX_M];
@@ -327,6 +328,7 @@ struct Ctx {
 
   // FGMRES storage
   int m = 30, max_it = 1000, reorth = 0;
+  double reorth_eta = 0.1;
   double rtol = 1e-10;
   int64_t N = 0;            // s * n
   double* V = nullptr;      // (m+1) * N

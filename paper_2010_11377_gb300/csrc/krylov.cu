@@ -1,8 +1,8 @@
 // FP64 kernels of the outer solve: the Kronecker operator of Section 4,
 // A z = (I_s (x) M + h A (x) F) z, the stage right-hand side of
 // Eq. block_coeff_mtx, restarted right-preconditioned flexible GMRES with
-// classical Gram-Schmidt (reorthogonalised when the projected norm drops below
-// 1/sqrt(2) of the original), the IRK update u_{n+1} = u_n + h sum_i b_i k_i
+// classical Gram-Schmidt (a second pass when the projected norm drops below
+// eta of the original, eta = 0.1 by default), the IRK update u_{n+1} = u_n + h sum_i b_i k_i
 // (Section 2), and the discrete adjoint kernels.
 //
 // All FGMRES control lives on the device (GmresState): the index j, the
@@ -347,7 +347,7 @@ k_gs_axpy(GmresState* st, double* __restrict__ V, int64_t ldv, int64_t N, double
   if (last_block(st)) {
     if (threadIdx.x == 0) {
       double n2 = gather_partials(partials, 0);
-      if (PASS == 0 && (st->force_reorth || n2 < 0.5 * st->wnorm2)) {
+      if (PASS == 0 && (st->eta2 < 0.0 || n2 < st->eta2 * st->wnorm2)) {
         st->reorth = 1;
       } else {
         st->reorth = 0;
@@ -400,14 +400,14 @@ __global__ void k_loop_ctrl(GmresState* st, cudaGraphConditionalHandle h) {
 // ---------------------------------------------------------------------------
 // Right-hand sides and FGMRES initialisation (x = 0, V_0 = b, sigma_0 = 1/||b||)
 // ---------------------------------------------------------------------------
-__device__ void gmres_init_last(GmresState* st, double* partials, int m, int max_it, double rtol, int force) {
+__device__ void gmres_init_last(GmresState* st, double* partials, int m, int max_it, double rtol, double eta2) {
   if (threadIdx.x == 0) {
     double beta = sqrt(gather_partials(partials, 0));
     st->bnorm = beta;
     st->rtol = rtol;
     st->m = m;
     st->max_it = max_it;
-    st->force_reorth = force;
+    st->eta2 = eta2;
     st->j = 0;
     st->it = 0;
     st->restarts = 0;
@@ -430,7 +430,7 @@ template <int S>
 __global__ void __launch_bounds__(BS)
 k_rhs_forward(int n, SellView<double> Fv, const double* __restrict__ u, const double* __restrict__ g,
               double* __restrict__ b, double* __restrict__ V0, double* __restrict__ x, GmresState* st,
-              double* __restrict__ partials, int m, int max_it, double rtol, int force) {
+              double* __restrict__ partials, int m, int max_it, double rtol, double eta2) {
   pdl_trigger();
   pdl_wait();
   double nrm = 0.0;
@@ -454,7 +454,7 @@ k_rhs_forward(int n, SellView<double> Fv, const double* __restrict__ u, const do
   }
   double v[1] = {nrm};
   block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
-  if (last_block(st)) gmres_init_last(st, partials, m, max_it, rtol, force);
+  if (last_block(st)) gmres_init_last(st, partials, m, max_it, rtol, eta2);
 }
 
 // adjoint: b_i = h b_i lambda (the right-hand side of A^T mu = h (b (x) lambda))
@@ -462,7 +462,7 @@ template <int S>
 __global__ void __launch_bounds__(BS)
 k_rhs_adjoint(int n, KronCoef hb, const double* __restrict__ lam, double* __restrict__ b,
               double* __restrict__ V0, double* __restrict__ x, GmresState* st, double* __restrict__ partials,
-              int m, int max_it, double rtol, int force) {
+              int m, int max_it, double rtol, double eta2) {
   pdl_trigger();
   pdl_wait();
   double nrm = 0.0;
@@ -479,7 +479,7 @@ k_rhs_adjoint(int n, KronCoef hb, const double* __restrict__ lam, double* __rest
   }
   double v[1] = {nrm};
   block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
-  if (last_block(st)) gmres_init_last(st, partials, m, max_it, rtol, force);
+  if (last_block(st)) gmres_init_last(st, partials, m, max_it, rtol, eta2);
 }
 
 // u += sum_i (h b_i) k_i   (Section 2)
@@ -762,10 +762,13 @@ void set_loop_condition_launch(Ctx& c, cudaGraphConditionalHandle h, cudaStream_
   CK_LAUNCH();
 }
 
+// the second-pass test of the Gram-Schmidt kernels: eta^2, or -1 for "always"
+static double reorth_eta2(const Ctx& c) { return c.reorth == 1 ? -1.0 : c.reorth_eta * c.reorth_eta; }
+
 void rhs_forward_launch(Ctx& c, const double* u, cudaStream_t st) {
   IRK_DISPATCH_S(c.s, {
     launch_k(k_rhs_forward<S>, row_grid(c), BS, 0, st, c.n, view<double>(c.Fs), u, c.g, c.bv, c.V, c.x, c.st, c.partials,
-                                                 c.m, c.max_it, c.rtol, c.reorth);
+                                                 c.m, c.max_it, c.rtol, reorth_eta2(c));
   });
   CK_LAUNCH();
 }
@@ -776,7 +779,7 @@ void rhs_adjoint_launch(Ctx& c, const double* lam, cudaStream_t st) {
   for (int i = 0; i < c.s; ++i) hb.a[i] = c.h * c.b[i];
   IRK_DISPATCH_S(c.s, {
     launch_k(k_rhs_adjoint<S>, row_grid(c), BS, 0, st, c.n, hb, lam, c.bv, c.V, c.x, c.st, c.partials, c.m, c.max_it,
-                                                 c.rtol, c.reorth);
+                                                 c.rtol, reorth_eta2(c));
   });
   CK_LAUNCH();
 }
