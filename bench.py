@@ -189,7 +189,9 @@ def roofline(ctx, s, its_per_step, traffic_file):
     from paper_2010_11377_gb300 import binding as B
     pk, src = peaks()
     hbm = pk["hbm_gbs"]
-    jm = max(1, min(29, int(round(its_per_step / 2))))   # mean basis index of an iteration
+    # mean basis index of an iteration: FGMRES(30) restarts at j = 0 every 30 iterations
+    nit = max(1, int(round(its_per_step)))
+    jm = max(1, min(29, int(round(sum(i % 30 for i in range(nit)) / nit))))
     prof = {}
     for tgt, j in (("smooth0", 0), ("kron", 0), ("precond", 0), ("vcycle", 0), ("gs_dots", jm), ("gs_axpy", jm)):
         r = B.irk_profile(ctx, tgt, j=j, warm=3, reps=20)
@@ -383,6 +385,75 @@ def run_kernel(args):
     ctx.close()
 
 
+def run_sweep(args):
+    """Configuration sweeps, one JSON line per run (right-preconditioned
+    FGMRES(30), FP32 AMG unless stated; `--sweep-steps` timed steps after one
+    untimed step, times per step from CUDA events):
+      c2  heat N in {256, 512, 1024}, Radau IIA s in {3, 5, 7}, h_t = 1/64, J / GSL / GSL_OPT / DU / LD
+      c3  double glazing N in {256, 512, 1024}, s = 2..7, h_t = 0.01, GSL / LD
+      c4  N = 1024, s = 5, LD: AMG in FP64 / FP32 / BF16-finest, heat and double glazing
+      ht  heat N = 128, s in {2, 7}, h_t in {0.05, 0.1, 0.5, 1, 5}, GSL / LD, rtol 1e-8"""
+    import numpy as np
+    import torch
+    import synth
+    from __graft_entry__ import build
+    build()
+    from paper_2010_11377_gb300 import binding as B
+    from paper_2010_11377_gb300 import problems
+    steps = args.sweep_steps
+
+    def run(p, s, h, kind, u0, prec="f32", rtol=1e-10, tag=""):
+        A, b, c = B.irk_butcher_table("radau_iia", s)
+        o = B.irk_default_options(kind=kind, amg_prec=prec, rtol=rtol)
+        t0 = time.perf_counter()
+        ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o, g=p["g"])
+        setup = time.perf_counter() - t0
+        u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+        out = torch.empty_like(u)
+        B.irk_run(ctx, u, 1, out)
+        torch.cuda.synchronize()
+        st = B.irk_run(ctx, u, steps, out)
+        rows, _ = B.irk_amg_info(ctx, 0)
+        ms = st["ms"] / steps
+        print(json.dumps({"sweep": tag, "problem": p["kind"], "N": p["N"], "n": p["n"], "s": s, "h_t": h,
+                          "precond": kind, "amg": prec, "rtol": rtol, "its_per_step": st["iterations"] / steps,
+                          "max_step_its": st["max_step_iterations"], "ms_per_step": round(ms, 3),
+                          "value": s * p["n"] / (ms * 1e-3), "resid": st["resid"], "setup_s": round(setup, 3),
+                          "amg_rows": rows}), flush=True)
+        ctx.close()
+
+    if args.sweep == "c2":
+        for N in (256, 512, 1024):
+            p = problems.heat(N)
+            u0 = synth.heat_u0(p["mesh"])
+            for s in (3, 5, 7):
+                for kind in ("J", "GSL", "GSL_OPT", "DU", "LD"):
+                    run(p, s, 1.0 / 64, kind, u0, tag="c2")
+    elif args.sweep == "c3":
+        for N in (256, 512, 1024):
+            p = problems.double_glazing(N)
+            u0 = np.zeros(p["n"])
+            for s in (2, 3, 4, 5, 6, 7):
+                for kind in ("GSL", "LD"):
+                    run(p, s, 0.01, kind, u0, tag="c3")
+    elif args.sweep == "c4":
+        p = problems.heat(1024)
+        u0 = synth.heat_u0(p["mesh"])
+        for prec in ("f64", "f32", "bf16"):
+            run(p, 5, 1.0 / 64, "LD", u0, prec, tag="c4")
+        p = problems.double_glazing(1024)
+        u0 = np.zeros(p["n"])
+        for prec in ("f64", "f32", "bf16"):
+            run(p, 5, 0.01, "LD", u0, prec, tag="c4")
+    elif args.sweep == "ht":
+        p = problems.heat(128)
+        u0 = synth.heat_u0(p["mesh"])
+        for s in (2, 7):
+            for h in (0.05, 0.1, 0.5, 1.0, 5.0):
+                for kind in ("GSL", "LD"):
+                    run(p, s, h, kind, u0, rtol=1e-8, tag="ht")
+
+
 def run_batch(args):
     """Batched uneven instances: 64 heat problems on grids 64^2..512^2 (N_i =
     32 round(2 8^(i/63))), per-element log-diffusion from a Gaussian random
@@ -489,6 +560,9 @@ def main():
     ap.add_argument("--kernel-j", type=int, default=22, help="Gram-Schmidt basis index for --kernel")
     ap.add_argument("--kernel-warm", type=int, default=3)
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht"],
+                    help="configuration sweep (one JSON line per run)")
+    ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--launch-list", action="store_true",
                     help="only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()
@@ -500,6 +574,8 @@ def main():
         run_batch(args)
     elif args.kernel:
         run_kernel(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -145,3 +145,30 @@ def test_fem_quad_rule_exact_degree4(L):
             # sum_k C[k, l] = int w . grad phi_l ; for l = 1 (phi = x): int x^a y^b
             exact = factorial(a) * factorial(bexp) / factorial(a + bexp + 2)
             assert abs(C[:, 1].sum() - exact) < 1e-14, (a, bexp)
+
+
+@pytest.mark.parametrize("field,value", [("reorth_eta", 1.0), ("reorth_eta", -0.1), ("reorth", 2),
+                                         ("restart", 0), ("coarse_max", 2048), ("cheb_degree", 0)])
+def test_setup_rejects_bad_options_before_device_work(L, field, value):
+    """Option validation happens on the host, before any CUDA call: a bad
+    option returns IRK_ERR_INVALID with a message and no context."""
+    import ctypes as C
+    from paper_2010_11377_gb300 import _abi as A
+    from paper_2010_11377_gb300.binding import irk_default_options
+    rowptr = np.array([0, 1], dtype=np.int64)
+    col = np.array([0], dtype=np.int32)
+    val = np.array([1.0])
+    Am, b, c = obt.radau_iia(2)
+    Am, b, c = (np.ascontiguousarray(x, dtype=np.float64) for x in (Am, b, c))
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    prob = A.IrkProblem()
+    prob.M = A.IrkCsr(1, 1, rowptr.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
+                      dp(val))
+    prob.F = prob.M
+    bt = A.IrkButcher(2, dp(Am), dp(b), dp(c))
+    o = irk_default_options()
+    setattr(o, field, value)
+    out = C.c_void_p()
+    st = L.irk_setup(C.byref(prob), C.byref(bt), 0.1, C.byref(o), None, C.byref(out))
+    assert st == 1 and not out.value
+    assert L.irk_last_error(None)

@@ -222,6 +222,26 @@ def test_heat_c1_run(kind):
         assert np.linalg.norm(host(ck[q]) - refs[5 * q]) <= 1e-8 * np.linalg.norm(refs[5 * q])
 
 
+@pytest.mark.parametrize("reorth,eta", [(1, 0.1), (0, 0.7071067811865476), (0, 0.1), (0, 0.0)])
+def test_gram_schmidt_second_pass_threshold(reorth, eta):
+    """The second Gram-Schmidt pass (always, 1/sqrt(2) rule, the default 0.1,
+    never) leaves the step within 1e-8 of the oracle's exact stage solve and
+    the FGMRES iteration counts within 10% of the oracle's MGS-FGMRES."""
+    mesh, prob = heat(60)
+    A, b, _ = obt.radau_iia(5)
+    h = 1 / 64
+    ctx, At = oracle_ctx(prob, A, "LD", h, amg_prec="f32", b=b, reorth=reorth, reorth_eta=eta, **AMG_OPTS)
+    u0 = synth.heat_u0(mesh)
+    ref = oirk.IRKSolver(prob, A, b, h, kind=None).step(u0, direct=True).u
+    oit = oirk.IRKSolver(prob, A, b, h, kind="LD", subsolve="amg", amg_opts=oracle_amg_opts(),
+                         Atilde=At).step(u0).iterations
+    out = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    st = B().irk_step(ctx, dev(u0), out)
+    assert np.linalg.norm(host(out) - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert st["resid"] <= 1e-10
+    assert _its_close(st["iterations"], oit), (st["iterations"], oit)
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
 def test_double_glazing_steps(prec):
     mesh, prob = dg(48)
