@@ -335,7 +335,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded P1 heat problem; u0 = sin(pi x) sin(pi y))",
         "config": {"workload": name, "grid": f"{N}x{N}", "n_per_stage": n, "stages": s, "method": "Radau IIA",
-                   "h_t": h, "precond": f"P_{kind}", "amg": prec + " V-cycle (Chebyshev 4, V(1,1), coarsest <= 1024 rows)",
+                   "h_t": h, "precond": f"P_{kind}", "amg": prec + " V-cycle (Chebyshev 4, V(1,1), coarsest <= 2048 rows)",
                    "krylov": "FGMRES(30) rtol 1e-10", "parallelism": f"replicas x{world}",
                    "l2": "working set > L2 (Krylov bases 1.3 GB); no flush"},
         "iterations_per_step": its, "resid": st["resid"], "setup_s": setup_s,

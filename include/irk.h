@@ -92,7 +92,7 @@ typedef struct {
   double cheb_lo;        /* lower end of the Chebyshev interval [lo, 1] of D_l1^{-1} A */
   int32_t nu_pre, nu_post; /* V(nu_pre, nu_post) sweeps */
   double theta;          /* strength threshold */
-  int32_t coarse_max;    /* coarsest level has at most this many rows (<= 1024) */
+  int32_t coarse_max;    /* coarsest level has at most this many rows (<= 2048) */
   int32_t max_levels;    /* <= 16 */
   int32_t restart;       /* FGMRES restart length m (1..64) */
   double rtol;           /* stop when ||b - A k||_2 <= rtol ||b||_2 */
@@ -138,7 +138,7 @@ irk_status irk_ldu(int32_t s, const double* A, double* L, double* D, double* U);
 irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, double* kappa);
 
 /* Fill *opt with the defaults: P_LD, FP32 AMG, Chebyshev degree 4 on [0.1, 1],
- * V(1,1), theta 0.08, coarse_max 1024, 12 levels, FGMRES(30), rtol 1e-10,
+ * V(1,1), theta 0.08, coarse_max 2048, 12 levels, FGMRES(30), rtol 1e-10,
  * max_it 1000, selective reorthogonalisation (reorth_eta 0.1). */
 void irk_default_options(irk_options* opt);
 

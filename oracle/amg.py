@@ -22,7 +22,7 @@ reading fixed in the design notes, step by step:
   P          tentative piecewise constant P_t (entries 1), smoothed once:
              P = (I - omega D^{-1} A) P_t, omega = 4 / (3 rho),
              rho = max_i sum_j |a_ij| / |a_ii|.
-  coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max (1024) or
+  coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max (2048) or
              coarsening stalls (the next level would keep more than 90% of the
              rows); the coarsest level is solved directly (dense LU) when it
              has at most coarse_max rows, otherwise by 4 smoothing sweeps from
@@ -163,7 +163,7 @@ class Level:
 class Hierarchy:
     """AMG hierarchy of one diagonal block."""
 
-    def __init__(self, A, theta=0.08, coarse_max=1024, max_levels=12,
+    def __init__(self, A, theta=0.08, coarse_max=2048, max_levels=12,
                  nu_pre=1, nu_post=1, smoother="chebyshev", cheb_degree=4,
                  cheb_lo=0.1):
         self.theta = theta

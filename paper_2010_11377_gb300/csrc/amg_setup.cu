@@ -17,7 +17,7 @@
 //              aggregate of its phase-1 strong neighbour of largest priority;
 //              aggregates numbered by increasing root index
 //   P          (I - omega D^{-1} A) P_tent, omega = 4/(3 max_i sum_j|a_ij|/|a_ii|)
-//   coarse     A_c = P^T A P by two deterministic SpGEMMs, until n <= coarse_max
+//   coarse     A_c = P^T A P by two deterministic SpGEMMs, until n <= coarse_max (2048)
 //              or coarsening stalls (a level would keep > 90% of its rows);
 //              the coarsest level is inverted densely (Gauss-Jordan, partial
 //              pivoting, FP64).

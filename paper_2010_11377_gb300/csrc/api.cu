@@ -377,7 +377,7 @@ void irk_default_options(irk_options* o) {
   o->nu_pre = 1;
   o->nu_post = 1;
   o->theta = 0.08;
-  o->coarse_max = 1024;
+  o->coarse_max = 2048;
   o->max_levels = 12;
   o->restart = 30;
   o->rtol = 1e-10;
@@ -423,7 +423,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (!(o.reorth_eta >= 0.0 && o.reorth_eta < 1.0) || o.reorth < 0 || o.reorth > 1)
     return set_err(nullptr, IRK_ERR_INVALID, "reorth must be 0 or 1 and 0 <= reorth_eta < 1");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
-    return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..1024");
+    return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..2048");
   const irk_csr& M = prob->M;
   const irk_csr& F = prob->F;
   if (M.n != F.n || M.nnz != F.nnz || M.n < 1) return set_err(nullptr, IRK_ERR_INVALID, "M and F differ in size");

@@ -27,7 +27,7 @@ constexpr int SELL_C = 32;
 constexpr int MAX_S = 8;
 constexpr int MAX_M = 64;
 constexpr int MAX_LEVELS = 16;
-constexpr int MAX_COARSE = 1024;
+constexpr int MAX_COARSE = 2048;
 
 struct Error {
   irk_status st;
@@ -203,7 +203,7 @@ struct Hier {
 
 struct AmgParams {
   double theta = 0.08;
-  int coarse_max = 1024;
+  int coarse_max = 2048;
   int max_levels = 12;
   int smoother = IRK_SMOOTH_CHEBYSHEV;
   int cheb_degree = 4;
