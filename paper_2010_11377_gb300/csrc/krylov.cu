@@ -22,18 +22,34 @@ constexpr int BS = 256;         // threads per block of the outer kernels
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
 // Exact FP32 -> FP64 widening by IEEE-754 field arithmetic on the integer
-// pipe (the conversion instruction shares the narrow FP64 pipe with the
+// pipe only (the conversion instruction shares the narrow FP64 pipe with the
 // DFMAs of the operator).  Normal numbers: sign kept, exponent re-biased by
-// 1023 - 127 = 896, the 23 fraction bits become the top of the 52.  Zero,
-// subnormal, infinite and NaN inputs take the conversion instruction.
+// 1023 - 127 = 896, the 23 fraction bits become the top of the 52.  Zero keeps
+// its sign; a subnormal m 2^-149 is normalised (leading one of m at bit p gives
+// exponent p - 149); infinities and NaNs keep their fraction bits.
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) {
-  unsigned u = __float_as_uint(x);
-  unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return static_cast<double>(x);
-  unsigned m = u & 0x7fffffu;
-  unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
-  return __hiloint2double(static_cast<int>(hi), static_cast<int>(m << 29));
+  const unsigned u = __float_as_uint(x);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x7fffffu;
+  unsigned hi, lo;
+  if (e == 0xffu) {
+    hi = sign | 0x7ff00000u | (m >> 3);
+    lo = m << 29;
+  } else if (e != 0u) {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (m == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else {
+    const int p = 31 - __clz(static_cast<int>(m));
+    const unsigned long long f = (static_cast<unsigned long long>(m) << (52 - p)) & 0xfffffffffffffull;
+    hi = sign | (static_cast<unsigned>(p - 149 + 1023) << 20) | static_cast<unsigned>(f >> 32);
+    lo = static_cast<unsigned>(f);
+  }
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
 
 // Sum C <= 16 per-thread values over the block; thread t < C writes slot t.
