@@ -222,6 +222,31 @@ def test_heat_c1_run(kind):
         assert np.linalg.norm(host(ck[q]) - refs[5 * q]) <= 1e-8 * np.linalg.norm(refs[5 * q])
 
 
+@pytest.mark.parametrize("kind", ["GSL", "DU", "LD"])
+@pytest.mark.parametrize("s", [2, 4])
+def test_lobatto_iiic_steps(kind, s):
+    """Lobatto IIIC through the same path (the library's own Butcher table):
+    3 steps within 1e-8 of the oracle's exact stage solves, iteration counts
+    within 10% of the oracle's FGMRES with the same AMG reading."""
+    mesh, prob = heat(44)
+    A, b, _ = obt.lobatto_iiic(s)
+    Al, bl, cl = B().irk_butcher_table("lobatto_iiic", s)
+    assert np.allclose(Al, A, atol=1e-14) and np.allclose(bl, b, atol=1e-14)
+    h = 1 / 32
+    ctx, At = oracle_ctx(prob, A, kind, h, amg_prec="f32", b=b, **AMG_OPTS)
+    u0 = synth.heat_u0(mesh)
+    refs, _ = oirk.IRKSolver(prob, A, b, h, kind=None).run(u0, 3, direct=True)
+    amg_sol = oirk.IRKSolver(prob, A, b, h, kind=kind, subsolve="amg", amg_opts=oracle_amg_opts(), Atilde=At)
+    u = dev(u0)
+    for t in range(3):
+        out = torch.empty_like(u)
+        st = B().irk_step(ctx, u, out)
+        err = np.linalg.norm(host(out) - refs[t + 1]) / np.linalg.norm(refs[t + 1])
+        assert err < 1e-8, (t, err)
+        assert _its_close(st["iterations"], amg_sol.step(refs[t]).iterations)
+        u = out
+
+
 @pytest.mark.parametrize("reorth,eta", [(1, 0.1), (0, 0.7071067811865476), (0, 0.1), (0, 0.0)])
 def test_gram_schmidt_second_pass_threshold(reorth, eta):
     """The second Gram-Schmidt pass (always, 1/sqrt(2) rule, the default 0.1,
