@@ -189,6 +189,72 @@ def fgmres(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000):
         restarts += 1
 
 
+def gmres_left(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000):
+    """Left-preconditioned restarted GMRES on P^{-1} A x = P^{-1} b from x0 = 0
+    (the left-preconditioned runs of Section 5): stop when the preconditioned
+    residual ||P^{-1}(b - A x)||_2 <= rtol ||P^{-1} b||_2.
+
+    Each cycle: r = P^{-1}(b - A x) formed explicitly, v_0 = r / ||r||; for j:
+    w = P^{-1} A v_j, MGS against v_0..v_j, Givens rotations, estimate
+    |g_{j+1}|; the cycle ends at j = m or when the estimate meets the
+    tolerance; x += V y.  `history` holds the explicit preconditioned
+    residual at every cycle start."""
+    shape = b.shape
+    bv = b.ravel()
+    r = apply_Pinv(b).ravel()
+    bnorm = np.linalg.norm(r)
+    x = np.zeros_like(bv)
+    if bnorm == 0.0:
+        return GmresResult(x.reshape(shape), 0, 0, 0.0, True, [])
+    it = 0
+    restarts = 0
+    history = []
+    while True:
+        beta = np.linalg.norm(r)
+        history.append(beta / bnorm)
+        if beta <= rtol * bnorm:
+            return GmresResult(x.reshape(shape), it, restarts, beta / bnorm, True, history)
+        if it >= max_it:
+            return GmresResult(x.reshape(shape), it, restarts, beta / bnorm, False, history)
+        V = np.zeros((m + 1, bv.size))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            w = apply_Pinv(apply_A(V[j].reshape(shape))).ravel()
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] != 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / den
+            sn[j] = H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            k = j + 1
+            if abs(g[j + 1]) <= rtol * bnorm or it >= max_it:
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + V[:k].T @ y
+        r = apply_Pinv((bv - apply_A(x.reshape(shape)).ravel()).reshape(shape)).ravel()
+        restarts += 1
+
+
 # ----------------------------------------------------------------------------
 # Section 2: one IRK step  u_{n+1} = u_n + h sum_i b_i K_i
 # ----------------------------------------------------------------------------
@@ -205,7 +271,7 @@ class IRKSolver:
     """One problem (M, F, g), one Butcher table, one time step h."""
 
     def __init__(self, prob, A, b, h, kind="LD", subsolve="amg", m=30,
-                 rtol=1e-10, amg_opts=None, Atilde=None):
+                 rtol=1e-10, amg_opts=None, Atilde=None, side="right"):
         self.M, self.F, self.g = prob.M, prob.F, prob.g
         self.A = np.asarray(A, dtype=np.float64)
         self.b = np.asarray(b, dtype=np.float64)
@@ -213,6 +279,9 @@ class IRKSolver:
         self.s = self.A.shape[0]
         self.m, self.rtol = m, rtol
         self.kind = kind
+        if side not in ("right", "left"):
+            raise ValueError("side must be 'right' or 'left'")
+        self.side = side
         self.subsolve = subsolve
         self.amg_opts = amg_opts
         self.pc = None
@@ -229,8 +298,8 @@ class IRKSolver:
         return apply_operator(self.M.T.tocsr(), self.F.T.tocsr(), self.A.T, self.h, z)
 
     def solve_stages(self, rhs):
-        res = fgmres(self.op, self.pc.apply, rhs, m=self.m, rtol=self.rtol)
-        return res
+        solver = gmres_left if self.side == "left" else fgmres
+        return solver(self.op, self.pc.apply, rhs, m=self.m, rtol=self.rtol)
 
     def solve_stages_direct(self, rhs):
         K = kron_matrix(self.M, self.F, self.A, self.h)

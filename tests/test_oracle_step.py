@@ -182,3 +182,57 @@ def test_fgmres_direct_subsolve_counts_c1():
     sol = irk.IRKSolver(prob, A, b, 0.05, kind="LD", subsolve="amg")
     st = sol.step(synth.heat_u0(mesh))
     assert np.linalg.norm(st.u - direct) <= 1e-9 * np.linalg.norm(direct)
+
+
+def _dense_pinv_op(sol, shape):
+    """P^{-1} A and the map v -> P^{-1} v as dense matrices (tiny problems)."""
+    n = int(np.prod(shape))
+    Pinv = np.column_stack([sol.pc.apply(e.reshape(shape)).ravel() for e in np.eye(n)])
+    A = np.column_stack([sol.op(e.reshape(shape)).ravel() for e in np.eye(n)])
+    return Pinv, A
+
+
+@pytest.mark.parametrize("kind", ["GSL", "LD"])
+def test_left_gmres_minimises_preconditioned_residual(kind):
+    """After k iterations (one cycle, no restart) left-preconditioned GMRES
+    returns the x in K_k(P^{-1}A, P^{-1}b) minimising ||P^{-1}(b - A x)||_2:
+    the definition, solved here as a dense least-squares problem over an
+    orthonormal Krylov basis (with AMG subsolves, so P^{-1}A is not I)."""
+    mesh, prob = _heat(7)
+    A, b, _ = bt.radau_iia(3)
+    sol = irk.IRKSolver(prob, A, b, 0.05, kind=kind, subsolve="amg", side="left",
+                        amg_opts=dict(coarse_max=8))
+    rhs = irk.stage_rhs(prob.F, prob.g, synth.heat_u0(mesh), 3)
+    Pinv, Amat = _dense_pinv_op(sol, rhs.shape)
+    B = Pinv @ Amat
+    c = Pinv @ rhs.ravel()
+    for k in range(1, 6):
+        res = irk.gmres_left(sol.op, sol.pc.apply, rhs, m=30, rtol=1e-30, max_it=k)
+        K = np.column_stack([np.linalg.matrix_power(B, q) @ c for q in range(k)])
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(B @ Q, c, rcond=None)
+        x_ref = Q @ y
+        r_ref = np.linalg.norm(c - B @ x_ref) / np.linalg.norm(c)
+        assert res.iterations == k
+        assert abs(res.resid - r_ref) <= 1e-9 * max(r_ref, 1e-12) + 1e-14, (k, res.resid, r_ref)
+        assert np.linalg.norm(res.x.ravel() - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+
+
+def test_left_gmres_exact_preconditioner_and_solution():
+    """A~ = A with exact subsolves: P^{-1}A = I, one left iteration; with AMG
+    subsolves left and right GMRES reach the same stage solution."""
+    mesh, prob = _heat(8)
+    A, b, _ = bt.radau_iia(3)
+    P = irk.kron_matrix(prob.M, prob.F, A, 0.05)
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(P)
+    rhs = irk.stage_rhs(prob.F, prob.g, synth.heat_u0(mesh), 3)
+    sol = irk.IRKSolver(prob, A, b, 0.05, kind="LD", subsolve="direct", side="left")
+    res = irk.gmres_left(sol.op, lambda v: lu.solve(v.ravel()).reshape(v.shape), rhs)
+    assert res.iterations == 1
+    kex = sol.solve_stages_direct(rhs)
+    for side in ("left", "right"):
+        s2 = irk.IRKSolver(prob, A, b, 0.05, kind="LD", subsolve="amg", side=side, rtol=1e-12)
+        r = s2.solve_stages(rhs)
+        assert r.converged
+        assert np.linalg.norm(r.x - kex) <= 1e-9 * np.linalg.norm(kex)
