@@ -393,7 +393,9 @@ def run_sweep(args):
       c3  double glazing N in {256, 512, 1024}, s = 2..7, h_t = 0.01, GSL / LD
       c4  N = 1024, s = 5, LD: AMG in FP64 / FP32 / BF16-finest, heat and double glazing
       ht  heat N = 128, s in {2, 7}, h_t in {0.05, 0.1, 0.5, 1, 5}, GSL / LD, rtol 1e-8
-      lob heat N in {256, 1024}, Lobatto IIIC s in {2, 3, 4, 5}, h_t = 1/64, J / GSL / DU / LD"""
+      lob heat N in {256, 1024}, Lobatto IIIC s in {2, 3, 4, 5}, h_t = 1/64, J / GSL / DU / LD
+      htlr  as ht with FP64 AMG, left- and right-preconditioned (stop on the preconditioned /
+          the true residual respectively)"""
     import numpy as np
     import torch
     import synth
@@ -403,9 +405,9 @@ def run_sweep(args):
     from paper_2010_11377_gb300 import problems
     steps = args.sweep_steps
 
-    def run(p, s, h, kind, u0, prec="f32", rtol=1e-10, tag="", method="radau_iia"):
+    def run(p, s, h, kind, u0, prec="f32", rtol=1e-10, tag="", method="radau_iia", side="right"):
         A, b, c = B.irk_butcher_table(method, s)
-        o = B.irk_default_options(kind=kind, amg_prec=prec, rtol=rtol)
+        o = B.irk_default_options(kind=kind, amg_prec=prec, rtol=rtol, side=side)
         t0 = time.perf_counter()
         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o, g=p["g"])
         setup = time.perf_counter() - t0
@@ -416,7 +418,8 @@ def run_sweep(args):
         st = B.irk_run(ctx, u, steps, out)
         rows, _ = B.irk_amg_info(ctx, 0)
         ms = st["ms"] / steps
-        print(json.dumps({"sweep": tag, "problem": p["kind"], "method": method, "N": p["N"], "n": p["n"], "s": s, "h_t": h,
+        print(json.dumps({"sweep": tag, "problem": p["kind"], "method": method, "side": side, "N": p["N"], "n": p["n"],
+                          "s": s, "h_t": h,
                           "precond": kind, "amg": prec, "rtol": rtol, "its_per_step": st["iterations"] / steps,
                           "max_step_its": st["max_step_iterations"], "ms_per_step": round(ms, 3),
                           "value": s * p["n"] / (ms * 1e-3), "resid": st["resid"], "setup_s": round(setup, 3),
@@ -453,6 +456,14 @@ def run_sweep(args):
             for s in (2, 3, 4, 5):
                 for kind in ("J", "GSL", "DU", "LD"):
                     run(p, s, 1.0 / 64, kind, u0, tag="lob", method="lobatto_iiic")
+    elif args.sweep == "htlr":
+        p = problems.heat(128)
+        u0 = synth.heat_u0(p["mesh"])
+        for s in (2, 7):
+            for h in (0.05, 0.1, 0.5, 1.0, 5.0):
+                for side in ("left", "right"):
+                    for kind in ("GSL", "LD"):
+                        run(p, s, h, kind, u0, prec="f64", rtol=1e-8, tag="htlr", side=side)
     elif args.sweep == "ht":
         p = problems.heat(128)
         u0 = synth.heat_u0(p["mesh"])
@@ -568,7 +579,7 @@ def main():
     ap.add_argument("--kernel-j", type=int, default=22, help="Gram-Schmidt basis index for --kernel")
     ap.add_argument("--kernel-warm", type=int, default=3)
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob"],
+    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--launch-list", action="store_true",

@@ -102,6 +102,13 @@ typedef struct {
   double reorth_eta;     /* 0 <= reorth_eta < 1; 0: never a second pass.  Default 0.1: one
                             classical pass loses at most about eps/reorth_eta of orthogonality
                             per vector, so a second pass is taken only on heavy cancellation */
+  int32_t side;          /* 0: right-preconditioned flexible GMRES, stop on the true residual
+                            (default); 1: left-preconditioned GMRES on P^{-1} A k = P^{-1} b
+                            (the left-preconditioned runs of Section 5), stop on the
+                            preconditioned residual ||P^{-1}(b - A k)|| <= rtol ||P^{-1} b||.
+                            Left preconditioning needs a fixed linear P^{-1}: use FP64 AMG for
+                            rtol below the AMG precision.  Forward solves only: the adjoint
+                            entry points and batches reject side = 1 */
 } irk_options;
 
 typedef struct {

@@ -77,6 +77,8 @@ def irk_default_options(**overrides) -> IrkOptions:
             v = PC_KINDS[v.upper()] if isinstance(v, str) else v
         elif k == "amg_prec":
             v = AMG_PREC[v]
+        elif k == "side":
+            v = {"right": 0, "left": 1}[v] if isinstance(v, str) else v
         elif k == "smoother":
             v = SMOOTHERS[v] if isinstance(v, str) else v
         setattr(o, k, v)

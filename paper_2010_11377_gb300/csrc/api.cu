@@ -104,6 +104,7 @@ static void alloc_solver_buffers(Ctx& c) {
   c.Z = c.pool.alloc(es * size_t(c.m) * c.N);
   c.x = c.pool.get<double>(c.N);
   c.bv = c.pool.get<double>(c.N);
+  c.T = c.side == 1 ? c.pool.get<double>(c.N) : nullptr;
   c.u = c.pool.get<double>(c.n);
   c.lam = c.pool.get<double>(c.n);
   c.tmpn = c.pool.get<double>(c.n);
@@ -159,16 +160,22 @@ static void build_graph(Ctx& c, bool adjoint) {
   cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   cudaGraph_t graph;
   CK(cudaGraphCreate(&graph, 0));
+  const bool left = !adjoint && c.side == 1;
+  int64_t fixed = 3;
   // head
   CK(cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, mode));
   if (adjoint) rhs_adjoint_launch(c, c.lam, st);
   else rhs_forward_launch(c, c.u, st);
+  if (left) fixed += left_head_launch(c, st);
+  std::vector<cudaGraphNode_t> head;   // the captured nodes the loop follows
+  {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+    head.assign(deps, deps + nd);
+  }
   CK(cudaStreamEndCapture(st, &graph));
-  size_t nn = 0;
-  CK(cudaGraphGetNodes(graph, nullptr, &nn));
-  std::vector<cudaGraphNode_t> nodes(nn);
-  CK(cudaGraphGetNodes(graph, nodes.data(), &nn));
-  cudaGraphNode_t head = nodes.back();
   // loop
   cudaGraphConditionalHandle handle;
   CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
@@ -178,17 +185,23 @@ static void build_graph(Ctx& c, bool adjoint) {
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t loop;
-  CK(cudaGraphAddNode(&loop, graph, &head, nullptr, 1, &cp));
+  CK(cudaGraphAddNode(&loop, graph, head.data(), nullptr, head.size(), &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
-  PrecondArgs pa{c.V, &c.st->j, c.N, c.st->sigma, c.Z, c.N, &c.st->done};
-  int64_t nb = precond_launch(c, pa, adjoint, st);
-  nb += fgmres_body_launch(c, adjoint, st);
+  int64_t nb = 0;
+  if (left) {
+    nb += left_body_launch(c, st);
+  } else {
+    PrecondArgs pa{c.V, &c.st->j, c.N, c.st->sigma, c.Z, c.N, &c.st->done};
+    nb += precond_launch(c, pa, adjoint, st);
+    nb += fgmres_body_launch(c, adjoint, st);
+  }
   set_loop_condition_launch(c, handle, st);
   nb += 1;
   CK(cudaStreamEndCapture(st, &body));
   // tail
   CK(cudaStreamBeginCaptureToGraph(st, graph, &loop, nullptr, 1, mode));
+  if (left) fixed += left_tail_launch(c, st);
   if (adjoint) adjoint_lambda_launch(c, c.lam, c.tmpn, st);
   else stage_update_launch(c, c.u, st);
   record_launch(c, st);
@@ -196,7 +209,7 @@ static void build_graph(Ctx& c, bool adjoint) {
   CK(cudaGraphInstantiate(&G.exec, graph, 0));
   G.graph = graph;
   G.body_kernels = nb;
-  G.fixed_kernels = 3;
+  G.fixed_kernels = fixed;
   G.conditional = true;
 }
 
@@ -209,17 +222,24 @@ static void launch_solve(Ctx& c, bool adjoint) {
     return;
   }
   cudaStream_t st = c.stream;
+  const bool left = !adjoint && c.side == 1;
   if (adjoint) rhs_adjoint_launch(c, c.lam, st);
   else rhs_forward_launch(c, c.u, st);
   int64_t k = 1;
+  if (left) k += left_head_launch(c, st);
   for (int it = 0; it < c.max_it + 8; ++it) {
-    PrecondArgs pa{c.V, &c.st->j, c.N, c.st->sigma, c.Z, c.N, &c.st->done};
-    k += precond_launch(c, pa, adjoint, st);
-    k += fgmres_body_launch(c, adjoint, st);
+    if (left) {
+      k += left_body_launch(c, st);
+    } else {
+      PrecondArgs pa{c.V, &c.st->j, c.N, c.st->sigma, c.Z, c.N, &c.st->done};
+      k += precond_launch(c, pa, adjoint, st);
+      k += fgmres_body_launch(c, adjoint, st);
+    }
     CK(cudaMemcpyAsync(c.h_flag, &c.st->done, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (*c.h_flag) break;
   }
+  if (left) k += left_tail_launch(c, st);
   if (adjoint) adjoint_lambda_launch(c, c.lam, c.tmpn, st);
   else stage_update_launch(c, c.u, st);
   record_launch(c, st);
@@ -289,6 +309,7 @@ static irk_status adjoint_one(Ctx& c, const double* lam_in, const double* u_n, c
 }
 
 static void check_adjoint_ok(Ctx& c, bool need_grad) {
+  if (c.side != 0) fail(IRK_ERR_INVALID, "the adjoint runs right-preconditioned contexts only (side = 0)");
   if (!c.symmetric) fail(IRK_ERR_INVALID, "adjoint needs symmetric M and F (transposed hierarchies are not built)");
   if (need_grad && c.n_tri == 0) fail(IRK_ERR_INVALID, "kappa gradient needs the mesh in irk_setup");
 }
@@ -384,6 +405,7 @@ void irk_default_options(irk_options* o) {
   o->max_it = 1000;
   o->reorth = 0;
   o->reorth_eta = 0.1;
+  o->side = 0;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -422,6 +444,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (!(o.rtol > 0.0) || o.max_it < 1) return set_err(nullptr, IRK_ERR_INVALID, "bad rtol/max_it");
   if (!(o.reorth_eta >= 0.0 && o.reorth_eta < 1.0) || o.reorth < 0 || o.reorth > 1)
     return set_err(nullptr, IRK_ERR_INVALID, "reorth must be 0 or 1 and 0 <= reorth_eta < 1");
+  if (o.side != 0 && o.side != 1) return set_err(nullptr, IRK_ERR_INVALID, "side must be 0 (right) or 1 (left)");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
     return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..2048");
   const irk_csr& M = prob->M;
@@ -455,6 +478,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     c.rtol = o.rtol;
     c.reorth = o.reorth;
     c.reorth_eta = o.reorth_eta;
+    c.side = o.side;
     c.kind = o.kind;
     c.amg.theta = o.theta;
     c.amg.coarse_max = o.coarse_max;

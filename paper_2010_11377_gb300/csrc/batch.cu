@@ -169,6 +169,7 @@ irk_status irk_batch_create(irk_ctx* const* ctxs, int32_t count, int32_t nsteps,
     for (int q = 0; q < count; ++q) {
       if (!ctxs[q] || ctxs[q]->c.device != dev) irk::fail(IRK_ERR_INVALID, "all batch contexts must share one device");
       if (!d_u0[q] || !d_uN[q] || !d_ckpt[q]) irk::fail(IRK_ERR_INVALID, "NULL instance buffer");
+      if (ctxs[q]->c.side != 0) irk::fail(IRK_ERR_INVALID, "batches run right-preconditioned contexts only");
       if (d_lambda && (!ctxs[q]->c.symmetric || (d_grad_kappa && d_grad_kappa[q] && ctxs[q]->c.n_tri == 0)))
         irk::fail(IRK_ERR_INVALID, "adjoint instances need symmetric M, F (and the mesh for kappa gradients)");
     }

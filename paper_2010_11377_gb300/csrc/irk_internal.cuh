@@ -235,6 +235,7 @@ struct GmresState {
   unsigned int counter;   // last-block-done ticket
   int guard;              // loop-body executions of this solve (bounded)
   double bnorm, rtol;
+  double bnorm_true;      // ||b|| (left preconditioning: bnorm is ||P^{-1} b||)
   double wnorm2;          // ||w||^2 before projection
   double eta2;            // second pass when ||w_proj||^2 < eta2 ||w||^2 (< 0: always)
   double resid;           // last true relative residual
@@ -331,6 +332,8 @@ struct Ctx {
   double reorth_eta = 0.1;
   double rtol = 1e-10;
   int64_t N = 0;            // s * n
+  int side = 0;             // 0: right-preconditioned FGMRES; 1: left-preconditioned GMRES
+  double* T = nullptr;      // N (left: A v_j, and the restart residual)
   double* V = nullptr;      // (m+1) * N
   void* Z = nullptr;        // m * N in the AMG precision
   double* x = nullptr;      // N
@@ -411,6 +414,12 @@ int precond_launch(Ctx& c, const PrecondArgs& a, bool transpose, cudaStream_t st
 
 // FGMRES pieces (krylov.cu)
 int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st);   // one iteration after P^{-1}
+// Left preconditioning (forward solves): after the right-hand side, P^{-1} b
+// and the first basis vector; one iteration w = P^{-1} A v_j including the
+// preconditioner; the true residual for the stats after the loop.
+int left_head_launch(Ctx& c, cudaStream_t st);
+int left_body_launch(Ctx& c, cudaStream_t st);
+int left_tail_launch(Ctx& c, cudaStream_t st);
 void set_loop_condition_launch(Ctx& c, cudaGraphConditionalHandle h, cudaStream_t st);
 void rhs_forward_launch(Ctx& c, const double* u, cudaStream_t st);
 void rhs_adjoint_launch(Ctx& c, const double* lam, cudaStream_t st);

@@ -420,6 +420,7 @@ __device__ void gmres_init_last(GmresState* st, double* partials, int m, int max
   if (threadIdx.x == 0) {
     double beta = sqrt(gather_partials(partials, 0));
     st->bnorm = beta;
+    st->bnorm_true = beta;
     st->rtol = rtol;
     st->m = m;
     st->max_it = max_it;
@@ -688,6 +689,174 @@ int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
   return launches;
 }
 
+// ---------------------------------------------------------------------------
+// Left-preconditioned GMRES on P^{-1} A k = P^{-1} b (x0 = 0), stopping on the
+// preconditioned residual.  The basis is built from w = P^{-1} A v_j; the
+// preconditioner output (AMG precision) is widened into the next basis slot.
+// A restart takes the residual P^{-1}(b - A x) = g_k V_{k+1} Q^T e_k from the
+// Givens rotations instead of another operator and preconditioner application.
+// ---------------------------------------------------------------------------
+
+// V_{j+1} = sigma_j P^{-1}(A V_j)   (P^{-1} applied to the unscaled A V_j)
+template <typename TZ>
+__global__ void __launch_bounds__(BS)
+k_left_widen(GmresState* st, const TZ* __restrict__ Zt, double* __restrict__ V, int64_t ldv, int64_t N) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done) return;
+  const int j = st->j;
+  const double sj = st->sigma[j];
+  double* __restrict__ w = V + int64_t(j + 1) * ldv;
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS)
+    w[e] = sj * to_f64(Zt[e]);
+}
+
+// first basis vector: Zt = P^{-1}(b / ||b||) -> V_0, ||P^{-1} b|| = ||V_0|| ||b||
+template <typename TZ>
+__global__ void __launch_bounds__(BS)
+k_left_start(GmresState* st, const TZ* __restrict__ Zt, double* __restrict__ V, int64_t N,
+             double* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done) return;
+  double nrm = 0.0;
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
+    double v = to_f64(Zt[e]);
+    V[e] = v;
+    nrm = fma(v, v, nrm);
+  }
+  double v1[1] = {nrm};
+  block_sum_store<1>(v1, partials + int64_t(blockIdx.x) * PL);
+  if (last_block(st)) {
+    if (threadIdx.x == 0) {
+      double n0 = sqrt(gather_partials(partials, 0));
+      double beta = n0 * st->bnorm;          // ||P^{-1} b||
+      st->bnorm_true = st->bnorm;
+      st->bnorm = beta;
+      st->sigma[0] = n0 > 0.0 ? 1.0 / n0 : 0.0;
+      st->g[0] = beta;
+      for (int i = 1; i <= MAX_M; ++i) st->g[i] = 0.0;
+      if (!(beta > 0.0) || !isfinite(beta)) {
+        st->status = isfinite(beta) ? IRK_OK : IRK_ERR_NONFINITE;
+        st->done = 1;
+        st->resid = 0.0;
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+// x += sum_i y_i sigma_i V_i at a cycle end (y from the triangular system)
+__global__ void __launch_bounds__(BS)
+k_left_xupdate(GmresState* st, const double* __restrict__ V, int64_t ldv, double* __restrict__ x, int64_t N) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done || !st->cycle_end) return;
+  __shared__ double y[MAX_M];
+  int k = st->j + 1;
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = st->g[i];
+      for (int q = i + 1; q < k; ++q) s -= st->H[q * (MAX_M + 1) + i] * y[q];
+      y[i] = s / st->H[i * (MAX_M + 1) + i];
+    }
+    for (int i = 0; i < k; ++i) y[i] *= st->sigma[i];
+  }
+  __syncthreads();
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
+    double xe = x[e];
+    for (int i = 0; i < k; ++i) xe = fma(y[i], V[int64_t(i) * ldv + e], xe);
+    x[e] = xe;
+  }
+}
+
+// cycle end: stop on the estimate |g_k| (or the iteration cap), else restart
+__global__ void k_left_decide(GmresState* st) {
+  pdl_trigger();
+  pdl_wait();
+  if (threadIdx.x || blockIdx.x) return;
+  if (st->done || !st->cycle_end) return;
+  int k = st->j + 1;
+  double est = fabs(st->g[k]);
+  st->resid = est / st->bnorm;
+  if (est <= st->rtol * st->bnorm || est == 0.0) {
+    st->done = 1;
+  } else if (st->it >= st->max_it) {
+    st->status = IRK_ERR_NOT_CONVERGED;
+    st->done = 1;
+  }
+}
+
+// restart residual r = g_k sum_i t_i sigma_i V_i with t = Q^T e_k, into T
+__global__ void __launch_bounds__(BS)
+k_left_residual(GmresState* st, const double* __restrict__ V, int64_t ldv, double* __restrict__ T, int64_t N,
+                double* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done || !st->cycle_end) return;
+  __shared__ double t[MAX_M + 1];
+  const int k = st->j + 1;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i <= k; ++i) t[i] = (i == k) ? 1.0 : 0.0;
+    for (int i = k - 1; i >= 0; --i) {   // t <- G_i^T t on rows (i, i+1)
+      double c = st->cs[i], s = st->sn[i];
+      double a = t[i], b = t[i + 1];
+      t[i] = c * a - s * b;
+      t[i + 1] = s * a + c * b;
+    }
+    double gk = st->g[k];
+    for (int i = 0; i <= k; ++i) t[i] *= gk * st->sigma[i];
+  }
+  __syncthreads();
+  double nrm = 0.0;
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) {
+    double r = 0.0;
+    for (int i = 0; i <= k; ++i) r = fma(t[i], V[int64_t(i) * ldv + e], r);
+    T[e] = r;
+    nrm = fma(r, r, nrm);
+  }
+  double v1[1] = {nrm};
+  block_sum_store<1>(v1, partials + int64_t(blockIdx.x) * PL);
+  if (last_block(st)) {
+    if (threadIdx.x == 0) {
+      double beta = sqrt(gather_partials(partials, 0));
+      st->wnorm2 = beta;   // handed to k_left_restart
+      st->counter = 0;
+    }
+  }
+}
+
+// V_0 = T, sigma_0 = 1/||T||, g = ||T|| e_0, next cycle
+__global__ void __launch_bounds__(BS)
+k_left_restart(GmresState* st, const double* __restrict__ T, double* __restrict__ V, int64_t N) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done || !st->cycle_end) return;
+  for (int64_t e = blockIdx.x * int64_t(BS) + threadIdx.x; e < N; e += int64_t(gridDim.x) * BS) V[e] = T[e];
+  if (last_block(st)) {
+    if (threadIdx.x == 0) {
+      double beta = st->wnorm2;
+      st->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+      st->g[0] = beta;
+      for (int i = 1; i <= MAX_M; ++i) st->g[i] = 0.0;
+      st->j = 0;
+      st->restarts += 1;
+      st->cycle_end = 0;
+      st->reorth = 0;
+      if (!(beta > 0.0)) st->done = 1;
+      st->counter = 0;
+    }
+  }
+}
+
+// true relative residual ||b - A x|| / ||b|| for the stats (after the loop)
+__global__ void k_left_final_resid(GmresState* st, const double* __restrict__ partials, int count) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s = 0.0;
+  for (int q = 0; q < count; ++q) s += partials[q];
+  st->resid = st->bnorm_true > 0.0 ? sqrt(s) / st->bnorm_true : 0.0;
+}
+
 // ||b - A k||_2: per-block partial sums of the squared residual, then one
 // block sums them in block order
 template <int S>
@@ -857,6 +1026,68 @@ void convert_launch(const void* in, int in_prec, void* out, int out_prec, int64_
   if (n <= 0) return;
   k_convert<<<nblk(n), 256, 0, st>>>(in, in_prec, out, out_prec, n);
   CK_LAUNCH();
+}
+
+}  // namespace irk
+
+namespace irk {
+
+int left_head_launch(Ctx& c, cudaStream_t st) {
+  // P^{-1} (sigma_0 V_0) = P^{-1} b / ||b|| into Z, then V_0 and the norms
+  PrecondArgs pa{c.V, &c.st->j, c.N, c.st->sigma, c.Z, 0, &c.st->done};
+  int launches = precond_launch(c, pa, false, st);
+  unsigned G = static_cast<unsigned>(c.gs_grid);
+  if (c.amg.amg_prec == 64)
+    launch_k(k_left_start<double>, G, BS, 0, st, c.st, static_cast<const double*>(c.Z), c.V, c.N, c.partials);
+  else
+    launch_k(k_left_start<float>, G, BS, 0, st, c.st, static_cast<const float*>(c.Z), c.V, c.N, c.partials);
+  CK_LAUNCH();
+  return launches + 1;
+}
+
+int left_body_launch(Ctx& c, cudaStream_t st) {
+  int n = c.n;
+  int64_t N = c.N;
+  unsigned G = static_cast<unsigned>(c.gs_grid);
+  const int* jp = &c.st->j;
+  int launches = 0;
+  // T = A V_j
+  IRK_DISPATCH_S(c.s, {
+    launch_k(k_kron<S, double, 0>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64,
+             JPtr<const double>{c.V, jp, N, 0, 0}, JPtr<double>{c.T, nullptr, 0, 0, 0}, c.K, nullptr, c.st,
+             c.partials);
+  });
+  ++launches;
+  // Z = P^{-1} T; V_{j+1} = sigma_j Z
+  PrecondArgs pa{c.T, nullptr, 0, nullptr, c.Z, 0, &c.st->done};
+  launches += precond_launch(c, pa, false, st);
+  if (c.amg.amg_prec == 64)
+    launch_k(k_left_widen<double>, G, BS, 0, st, c.st, static_cast<const double*>(c.Z), c.V, N, N);
+  else
+    launch_k(k_left_widen<float>, G, BS, 0, st, c.st, static_cast<const float*>(c.Z), c.V, N, N);
+  ++launches;
+  launch_k(k_gs_dots<0>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
+  launch_k(k_gs_axpy<0>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
+  launch_k(k_gs_dots<1>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
+  launch_k(k_gs_axpy<1>, G, BS, 0, st, c.st, c.V, N, N, c.partials);
+  launches += 4;
+  launch_k(k_left_xupdate, G, BS, 0, st, c.st, c.V, N, c.x, N);
+  launch_k(k_left_decide, 1, 32, 0, st, c.st);
+  launch_k(k_left_residual, G, BS, 0, st, c.st, c.V, N, c.T, N, c.partials);
+  launch_k(k_left_restart, G, BS, 0, st, c.st, c.T, c.V, N);
+  launches += 4;
+  CK_LAUNCH();
+  return launches;
+}
+
+int left_tail_launch(Ctx& c, cudaStream_t st) {
+  int grid = c.gs_grid;
+  IRK_DISPATCH_S(c.s, {
+    k_resid_partials<S><<<grid, BS, 0, st>>>(c.n, view<double>(c.Ms), c.Fs.v64, c.x, c.bv, c.K, c.partials);
+  });
+  k_left_final_resid<<<1, 32, 0, st>>>(c.st, c.partials, grid);
+  CK_LAUNCH();
+  return 2;
 }
 
 }  // namespace irk
