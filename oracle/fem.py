@@ -1,4 +1,4 @@
-"""P1 finite-element matrices (oracle; test infrastructure only).
+"""P1 and P2 finite-element matrices (oracle; test infrastructure only).
 
 Section 3 of the paper: after the weak form, the stage system involves the
 mass matrix M_kl = int phi_k phi_l and F, which is the stiffness
@@ -78,6 +78,60 @@ def assemble(xy, tri, kappa=None, wind=None):
         C.sum_duplicates()
         out["C"] = C
     return out
+
+
+def p2_basis(lam):
+    """Quadratic Lagrange basis at barycentric points lam (nq, 3), node order
+    (a, b, c, ab, bc, ca): vertex l_i (2 l_i - 1), edge 4 l_i l_j.  Returns
+    the values (nq, 6) and, per basis function, the coefficients of grad in
+    terms of grad l_0..l_2: D (nq, 6, 3) with grad phi_k = sum_i D[q,k,i] grad l_i."""
+    l0, l1, l2 = lam[:, 0], lam[:, 1], lam[:, 2]
+    nq = lam.shape[0]
+    phi = np.stack([l0 * (2 * l0 - 1), l1 * (2 * l1 - 1), l2 * (2 * l2 - 1),
+                    4 * l0 * l1, 4 * l1 * l2, 4 * l2 * l0], axis=1)
+    D = np.zeros((nq, 6, 3))
+    D[:, 0, 0] = 4 * l0 - 1
+    D[:, 1, 1] = 4 * l1 - 1
+    D[:, 2, 2] = 4 * l2 - 1
+    D[:, 3, 0], D[:, 3, 1] = 4 * l1, 4 * l0
+    D[:, 4, 1], D[:, 4, 2] = 4 * l2, 4 * l1
+    D[:, 5, 2], D[:, 5, 0] = 4 * l0, 4 * l2
+    return phi, D
+
+
+def assemble_p2(xy, tri6, kappa=None):
+    """Global CSR mass and stiffness of quadratic triangles (Section 5 runs
+    the heat problem with P2 elements).  The vertex columns of tri6 give the
+    affine map; integrals use the collapsed 3x3 Gauss rule (exact to degree
+    5, the mass integrand has degree 4)."""
+    nn = xy.shape[0]
+    nt = tri6.shape[0]
+    area, G = element_geometry(xy, tri6[:, :3])
+    if kappa is None:
+        kappa = np.ones(nt)
+    xi, eta, wq = _duffy_rule(3)
+    lam = np.stack([1.0 - xi - eta, xi, eta], axis=1)
+    phi, D = p2_basis(lam)
+    # int_T f = 2 |T| sum_q wq f(q)
+    Mref = 2.0 * np.einsum("q,qa,qb->ab", wq, phi, phi)            # per unit area
+    gradk = np.einsum("qki,eij->eqkj", D, G)                        # (nt, nq, 6, 2)
+    Ke = 2.0 * (kappa * area)[:, None, None] * np.einsum("q,eqaj,eqbj->eab", wq, gradk, gradk)
+    Me = area[:, None, None] * Mref[None]
+    rows = np.repeat(tri6, 6, axis=1).ravel()
+    cols = np.tile(tri6, (1, 6)).ravel()
+    M = sp.csr_matrix((Me.ravel(), (rows, cols)), shape=(nn, nn))
+    K = sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(nn, nn))
+    M.sum_duplicates()
+    K.sum_duplicates()
+    return {"M": M, "K": K}
+
+
+def heat_problem_p2(mesh, kappa=None):
+    """The heat problem of Section 3.1 with quadratic elements (Section 5)."""
+    mats = assemble_p2(mesh.xy, mesh.tri, kappa=kappa)
+    M = restrict(mats["M"], mesh.interior)
+    F = restrict(mats["K"], mesh.interior)
+    return Problem(M, F, np.zeros(mesh.n), mesh, kappa=kappa, kind="heat")
 
 
 def element_stiffness_unit(xy, tri):

@@ -18,7 +18,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "Mesh", "structured_mesh", "heat_u0", "double_glazing_wind",
+    "Mesh", "MeshP2", "structured_mesh", "structured_mesh_p2", "heat_u0", "double_glazing_wind",
     "double_glazing_boundary", "grf_log_kappa", "random_smooth_u0",
     "batch_instance_sizes", "random_stage_block",
 ]
@@ -80,6 +80,71 @@ class Mesh:
     @property
     def n(self) -> int:
         return self.interior.size
+
+
+class MeshP2:
+    """The same triangulation with quadratic (6-node) elements.
+
+    Nodes are the (2N+1)^2 points of the twice-refined lattice: node (I, J),
+    0 <= I, J <= 2N, has index J*(2N+1) + I and coordinates (x0 + I*hx/2,
+    y0 + J*hy/2); element vertices sit at even (I, J), edge midpoints at the
+    others.  Each triangle lists its nodes as (a, b, c, ab, bc, ca): the three
+    counter-clockwise vertices of the P1 mesh, then the midpoints of the edges
+    a-b, b-c, c-a.  Unknowns are the interior nodes, numbered row by row, so
+    n = (2N-1)^2 (the degrees of freedom per stage of the paper's P2 runs)."""
+
+    order = 2
+
+    def __init__(self, N: int, lo=(0.0, 0.0), hi=(1.0, 1.0)):
+        if N < 1:
+            raise ValueError("need N >= 1")
+        self.N = int(N)
+        self.lo = (float(lo[0]), float(lo[1]))
+        self.hi = (float(hi[0]), float(hi[1]))
+        m = 2 * N + 1
+        ii, jj = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+        ii = ii.ravel()
+        jj = jj.ravel()
+        hx = (self.hi[0] - self.lo[0]) / N
+        hy = (self.hi[1] - self.lo[1]) / N
+        self.hx, self.hy = hx, hy
+        self.xy = np.stack([self.lo[0] + ii * (0.5 * hx), self.lo[1] + jj * (0.5 * hy)], axis=1)
+        self.xy[ii == 2 * N, 0] = self.hi[0]
+        self.xy[jj == 2 * N, 1] = self.hi[1]
+        sq_i, sq_j = np.meshgrid(np.arange(N), np.arange(N), indexing="xy")
+        I0 = (2 * sq_i).ravel()
+        J0 = (2 * sq_j).ravel()
+
+        def node(di, dj):
+            return (J0 + dj) * m + (I0 + di)
+
+        t1 = np.stack([node(0, 0), node(2, 0), node(2, 2), node(1, 0), node(2, 1), node(1, 1)], axis=1)
+        t2 = np.stack([node(0, 0), node(2, 2), node(0, 2), node(1, 1), node(1, 2), node(0, 1)], axis=1)
+        self.tri = np.empty((2 * N * N, 6), dtype=np.int32)
+        self.tri[0::2] = t1
+        self.tri[1::2] = t2
+        self.boundary = (ii == 0) | (ii == 2 * N) | (jj == 0) | (jj == 2 * N)
+        self.dof = np.full(m * m, -1, dtype=np.int32)
+        interior = np.flatnonzero(~self.boundary)
+        self.dof[interior] = np.arange(interior.size, dtype=np.int32)
+        self.interior = interior
+
+    @property
+    def n_nodes(self) -> int:
+        return self.xy.shape[0]
+
+    @property
+    def n_tri(self) -> int:
+        return self.tri.shape[0]
+
+    @property
+    def n(self) -> int:
+        return self.interior.size
+
+
+def structured_mesh_p2(N: int) -> MeshP2:
+    """N x N squares of the unit square, each cut into two 6-node triangles."""
+    return MeshP2(N)
 
 
 def structured_mesh(N: int, domain: str = "unit") -> Mesh:

@@ -86,3 +86,48 @@ def test_problem_restriction():
     # hot east wall only
     east = mesh.xy[:, 0] == 1.0
     assert np.all(ub[east] == 1) and np.all(ub[~east] == 0)
+
+
+# ---------------------------------------------------------------------------
+# quadratic (P2) elements, the heat discretisation of the paper's runs
+# ---------------------------------------------------------------------------
+def test_p2_mesh_counts():
+    """(2N-1)^2 unknowns per stage: 225 at N = 8 and 961 at N = 16 (the DOF
+    column of the Radau IIA table divided by s: 450 / 2, 1922 / 2)."""
+    for N, n in ((8, 225), (16, 961), (128, 65025)):
+        m = synth.structured_mesh_p2(N)
+        assert m.n == n and m.tri.shape == (2 * N * N, 6) and m.n_nodes == (2 * N + 1) ** 2
+
+
+def test_p2_element_mass_closed_form():
+    """P2 mass matrix of one triangle: |T|/180 [[6,-1,-1,0,-4,0], ...] (node
+    order vertices, then midpoints of edges 01, 12, 20): the textbook closed
+    form, against the quadrature-based assembly."""
+    xy = np.array([[0.3, 0.1], [1.4, 0.5], [0.6, 1.2], [0.85, 0.3], [1.0, 0.85], [0.45, 0.65]])
+    tri = np.array([[0, 1, 2, 3, 4, 5]])
+    M = fem.assemble_p2(xy, tri)["M"].toarray()
+    area = 0.5 * abs((xy[1, 0] - xy[0, 0]) * (xy[2, 1] - xy[0, 1]) - (xy[2, 0] - xy[0, 0]) * (xy[1, 1] - xy[0, 1]))
+    ref = np.array([[6, -1, -1, 0, -4, 0], [-1, 6, -1, 0, 0, -4], [-1, -1, 6, -4, 0, 0],
+                    [0, 0, -4, 32, 16, 16], [-4, 0, 0, 16, 32, 16], [0, -4, 0, 16, 16, 32]]) * area / 180.0
+    assert np.abs(M - ref).max() <= 1e-14
+
+
+def test_p2_reproduces_quadratics():
+    """P2 Galerkin reproduces quadratic solutions exactly: -Lap u = f with
+    u = x^2 + 3xy - 2y^2 + x (f = -2) and Dirichlet data u: the interior
+    solution of K_II u_I = M_I f - K_IB u_B equals u at the nodes.  Checks the
+    whole P2 stiffness and mass assembly, boundary coupling included."""
+    mesh = synth.structured_mesh_p2(6)
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    u = x * x + 3 * x * y - 2 * y * y + x
+    f = -(2.0 - 4.0) * np.ones(mesh.n_nodes)
+    mats = fem.assemble_p2(mesh.xy, mesh.tri)
+    b = np.flatnonzero(mesh.boundary)
+    K_II, K_IB = fem.restrict(mats["K"], mesh.interior, b)
+    M_I = mats["M"].tocsr()[mesh.interior]
+    rhs = M_I @ f - K_IB @ u[b]
+    import scipy.sparse.linalg as spla
+    uI = spla.spsolve(K_II.tocsc(), rhs)
+    assert np.abs(uI - u[mesh.interior]).max() <= 1e-12
+    assert abs(mats["M"].sum() - 1.0) <= 1e-14
+    assert np.abs(mats["K"] @ np.ones(mesh.n_nodes)).max() <= 1e-12
