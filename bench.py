@@ -395,7 +395,9 @@ def run_sweep(args):
       ht  heat N = 128, s in {2, 7}, h_t in {0.05, 0.1, 0.5, 1, 5}, GSL / LD, rtol 1e-8
       lob heat N in {256, 1024}, Lobatto IIIC s in {2, 3, 4, 5}, h_t = 1/64, J / GSL / DU / LD
       htlr  as ht with FP64 AMG, left- and right-preconditioned (stop on the preconditioned /
-          the true residual respectively)"""
+          the true residual respectively)
+      t5  P2 heat, N in {8..128}, Radau IIA s = 2..7, h_t = h_x^(3/(2s-1)), manufactured
+          b = A k*, rtol 1e-8, J / GSL / DU / LD (the setting of the paper's Table 5)"""
     import numpy as np
     import torch
     import synth
@@ -456,6 +458,29 @@ def run_sweep(args):
             for s in (2, 3, 4, 5):
                 for kind in ("J", "GSL", "DU", "LD"):
                     run(p, s, 1.0 / 64, kind, u0, tag="lob", method="lobatto_iiic")
+    elif args.sweep == "t5":
+        # manufactured solutions on P2 heat matrices (the paper's Radau IIA table):
+        # b = A k* for a seeded k*, h_t = h_x^(3/(2s-1)), rtol 1e-8, one solve each
+        for s in (2, 3, 4, 5, 6, 7):
+            A, b, c = B.irk_butcher_table("radau_iia", s)
+            for N in (8, 16, 32, 64, 128):
+                p = problems.heat_p2(N)
+                h = (1.0 / N) ** (3.0 / (2 * s - 1))
+                kstar = torch.tensor(synth.random_stage_block(p["n"], s, 1000 + N).ravel(), device="cuda")
+                for kind in ("J", "GSL", "DU", "LD"):
+                    o = B.irk_default_options(kind=kind, rtol=1e-8)
+                    ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o)
+                    rhs = torch.empty_like(kstar)
+                    B.irk_apply_operator(ctx, kstar, rhs)
+                    k = torch.empty_like(kstar)
+                    B.irk_solve(ctx, rhs, k)                       # untimed first solve
+                    st = B.irk_solve(ctx, rhs, k)
+                    err = float((k - kstar).norm() / kstar.norm())
+                    print(json.dumps({"sweep": "t5", "problem": "heat_p2", "N": N, "n": p["n"], "s": s,
+                                      "dof": s * p["n"], "h_t": h, "precond": kind, "its": st["iterations"],
+                                      "ms": round(st["ms"], 3), "resid": st["resid"], "err_vs_kstar": err}),
+                          flush=True)
+                    ctx.close()
     elif args.sweep == "htlr":
         p = problems.heat(128)
         u0 = synth.heat_u0(p["mesh"])
@@ -579,7 +604,7 @@ def main():
     ap.add_argument("--kernel-j", type=int, default=22, help="Gram-Schmidt basis index for --kernel")
     ap.add_argument("--kernel-warm", type=int, default=3)
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr"],
+    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--launch-list", action="store_true",

@@ -150,7 +150,7 @@ irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, 
 void irk_default_options(irk_options* opt);
 
 /* ------------------------------------------------------------------------- *
- * P1 finite elements (Section 3), host side.                                 *
+ * P1 / P2 finite elements (Sections 3 and 5), host side.                     *
  * ------------------------------------------------------------------------- */
 
 /* Physical coordinates of the 6 quadrature points per triangle at which
@@ -172,6 +172,16 @@ irk_status irk_fem_assemble(int32_t n_nodes, const double* xy, int32_t n_tri, co
                             const int32_t* dof, int32_t n, const double* kappa, const double* wind,
                             const double* ub, int64_t* nnz, int64_t* rowptr, int32_t* col,
                             double* valM, double* valF, double* g);
+
+/* Quadratic (6-node) triangles for the heat problem, the discretisation of
+ * the paper's heat runs (Section 5): M_kl = int phi_k phi_l, F = sum_e
+ * kappa_e K_e with K_e the P2 stiffness.  tri6: n_tri*6 node indices per
+ * triangle, vertices counter-clockwise then the midpoints of edges ab, bc,
+ * ca (the vertices give the affine map).  Other arguments, the size query
+ * and the outputs as irk_fem_assemble (no wind). */
+irk_status irk_fem_assemble_p2(int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri6,
+                               const int32_t* dof, int32_t n, const double* kappa, const double* ub, int64_t* nnz,
+                               int64_t* rowptr, int32_t* col, double* valM, double* valF, double* g);
 
 /* ------------------------------------------------------------------------- *
  * Solver context.                                                            *
@@ -206,6 +216,14 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
  * IRK_ERR_NOT_CONVERGED / _BREAKDOWN / _NONFINITE from the device solve. */
 irk_status irk_step(irk_ctx* ctx, const double* d_u_n, double* d_u_np1, double* d_k,
                     irk_stats* stats);
+
+/* Solve the stage system (I_s (x) M + h A (x) F) k = b (Eq. block_coeff_mtx)
+ * for a given right-hand side with the context's preconditioner and Krylov
+ * method (the manufactured-solution runs of Section 5 solve it for
+ * b = A k* with a chosen k*).  d_b, d_k: s*n FP64 device vectors, stage-major
+ * [K_1; ...; K_s], caller-owned; d_k receives the solution.  Statistics and
+ * errors as irk_step (IRK_ERR_NOT_CONVERGED leaves the last iterate). */
+irk_status irk_solve(irk_ctx* ctx, const double* d_b, double* d_k, irk_stats* stats);
 
 /* nsteps steps from d_u0 (n) to d_u_out (n).  If d_ckpt is not NULL it
  * receives u at steps 0, ckpt_every, 2 ckpt_every, ... (row q = u_{q*ckpt_every},

@@ -114,6 +114,26 @@ def irk_fem_assemble(xy, tri, dof, n, kappa=None, wind=None, ub=None):
     return rowptr, col, valM, valF, g
 
 
+def irk_fem_assemble_p2(xy, tri6, dof, n, kappa=None, ub=None):
+    """Interior CSR (rowptr, col, valM, valF) and the lift g of quadratic triangles."""
+    L = lib()
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri6 = np.ascontiguousarray(tri6, dtype=np.int32)
+    dof = np.ascontiguousarray(dof, dtype=np.int32)
+    kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
+    ub = None if ub is None else np.ascontiguousarray(ub, dtype=np.float64)
+    nnz = C.c_int64(0)
+    args = (xy.shape[0], _dp(xy), tri6.shape[0], _ip(tri6), _ip(dof), n, _dp(kappa), _dp(ub))
+    check(L.irk_fem_assemble_p2(*args, C.byref(nnz), None, None, None, None, None))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    valM = np.zeros(nnz.value)
+    valF = np.zeros(nnz.value)
+    g = np.zeros(n)
+    check(L.irk_fem_assemble_p2(*args, C.byref(nnz), _lp(rowptr), _ip(col), _dp(valM), _dp(valF), _dp(g)))
+    return rowptr, col, valM, valF, g
+
+
 # ---------------------------------------------------------------------------
 # context
 # ---------------------------------------------------------------------------
@@ -190,6 +210,13 @@ def irk_setup(rowptr, col, valM, valF, butcher, h_t, options=None, g=None, mesh=
 def irk_step(ctx: Context, u_n, u_np1, k=None) -> dict:
     st = IrkStats()
     check(lib().irk_step(ctx.ptr, _dev(u_n), _dev(u_np1), _dev(k), C.byref(st)), ctx.ptr)
+    return st.as_dict()
+
+
+def irk_solve(ctx: Context, b, k) -> dict:
+    """Solve the stage system for the right-hand side b (s*n FP64, stage-major) into k."""
+    st = IrkStats()
+    check(lib().irk_solve(ctx.ptr, _dev(b), _dev(k), C.byref(st)), ctx.ptr)
     return st.as_dict()
 
 

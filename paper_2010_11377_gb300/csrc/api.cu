@@ -105,6 +105,8 @@ static void alloc_solver_buffers(Ctx& c) {
   c.x = c.pool.get<double>(c.N);
   c.bv = c.pool.get<double>(c.N);
   c.T = c.side == 1 ? c.pool.get<double>(c.N) : nullptr;
+  c.rhs_given = c.pool.get<int>(1);
+  CK(cudaMemset(c.rhs_given, 0, sizeof(int)));
   c.u = c.pool.get<double>(c.n);
   c.lam = c.pool.get<double>(c.n);
   c.tmpn = c.pool.get<double>(c.n);
@@ -560,6 +562,29 @@ irk_status irk_step(irk_ctx* h, const double* d_u_n, double* d_u_np1, double* d_
     CK(cudaEventRecord(c.ev_t1, c.stream));
     if (d_k) CK(cudaMemcpyAsync(d_k, c.x, sizeof(double) * c.N, cudaMemcpyDeviceToDevice, c.stream));
     CK(cudaMemcpyAsync(d_u_np1, c.u, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream));
+    irk::collect_stats(c, 1, stats, &dev, 0);
+    irk::end_call(c);
+  });
+  if (st != IRK_OK) return st;
+  if (dev != IRK_OK) return set_err(h, dev, std::string("device solve: ") + irk_status_string(dev));
+  return IRK_OK;
+}
+
+irk_status irk_solve(irk_ctx* h, const double* d_b, double* d_k, irk_stats* stats) {
+  if (!h || !d_b || !d_k) return set_err(h, IRK_ERR_INVALID, "NULL argument");
+  irk_status dev = IRK_OK;
+  irk_status st = guarded(h, [&] {
+    Ctx& c = h->c;
+    irk::build_graph(c, false);
+    irk::begin_call(c);
+    CK(cudaMemcpyAsync(c.bv, d_b, sizeof(double) * c.N, cudaMemcpyDeviceToDevice, c.stream));
+    CK(cudaMemsetAsync(c.rhs_given, 0x01, 1, c.stream));
+    irk::reset_records(c);
+    CK(cudaEventRecord(c.ev_t0, c.stream));
+    irk::launch_solve(c, false);
+    CK(cudaEventRecord(c.ev_t1, c.stream));
+    CK(cudaMemsetAsync(c.rhs_given, 0, sizeof(int), c.stream));
+    CK(cudaMemcpyAsync(d_k, c.x, sizeof(double) * c.N, cudaMemcpyDeviceToDevice, c.stream));
     irk::collect_stats(c, 1, stats, &dev, 0);
     irk::end_call(c);
   });

@@ -1,4 +1,5 @@
-// Host P1 assembly of the interior-unknown matrices of Section 3:
+// Host P1 (and, for the heat problem, P2) assembly of the interior-unknown
+// matrices of Section 3:
 //   M_kl = int phi_k phi_l,  F = sum_e kappa_e K_e + C,
 //   K_e[a,b] = |T| grad l_a . grad l_b,  C_kl = int phi_k (w . grad phi_l),
 // with strong Dirichlet elimination and the lift g = F_IB u_B.  The convection
@@ -164,6 +165,130 @@ irk_status irk_fem_assemble(int32_t n_nodes, const double* xy, int32_t n_tri, co
       int da = dof[t[a]];
       if (da < 0) continue;
       for (int b = 0; b < 3; ++b) {
+        int db = dof[t[b]];
+        if (db < 0) {
+          if (g && ub) g[da] += Fe[a][b] * ub[t[b]];
+          continue;
+        }
+        auto beg = cl.begin() + rp[da], end = cl.begin() + rp[da + 1];
+        int64_t pos = std::lower_bound(beg, end, db) - cl.begin();
+        valM[pos] += Me[a][b];
+        valF[pos] += Fe[a][b];
+      }
+    }
+  }
+  return IRK_OK;
+}
+
+// Quadratic (6-node) triangles for the heat problem of the paper's runs
+// (Section 5): M_e and K_e from the degree-4 rule (exact: the mass integrand
+// has degree 4, the stiffness integrand degree 2).  Basis at barycentric l:
+// vertex i: l_i (2 l_i - 1), edge (i, j): 4 l_i l_j, node order a, b, c, ab,
+// bc, ca.
+irk_status irk_fem_assemble_p2(int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri6,
+                               const int32_t* dof, int32_t n, const double* kappa, const double* ub, int64_t* nnz,
+                               int64_t* rowptr, int32_t* col, double* valM, double* valF, double* g) {
+  if (n_nodes <= 0 || n_tri <= 0 || n <= 0 || !xy || !tri6 || !dof || !nnz) {
+    irk::set_global_error("bad argument to irk_fem_assemble_p2");
+    return IRK_ERR_INVALID;
+  }
+  for (int64_t e = 0; e < 6 * int64_t(n_tri); ++e)
+    if (tri6[e] < 0 || tri6[e] >= n_nodes) {
+      irk::set_global_error("triangle node out of range");
+      return IRK_ERR_INVALID;
+    }
+  for (int v = 0; v < n_nodes; ++v)
+    if (dof[v] >= n) {
+      irk::set_global_error("dof index out of range");
+      return IRK_ERR_INVALID;
+    }
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (int e = 0; e < n_tri; ++e)
+    for (int a = 0; a < 6; ++a) {
+      int da = dof[tri6[6 * e + a]];
+      if (da < 0) continue;
+      for (int b = 0; b < 6; ++b)
+        if (dof[tri6[6 * e + b]] >= 0) ++cnt[da + 1];
+    }
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> raw(cnt[n]);
+  std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
+  for (int e = 0; e < n_tri; ++e)
+    for (int a = 0; a < 6; ++a) {
+      int da = dof[tri6[6 * e + a]];
+      if (da < 0) continue;
+      for (int b = 0; b < 6; ++b) {
+        int db = dof[tri6[6 * e + b]];
+        if (db >= 0) raw[cur[da]++] = db;
+      }
+    }
+  std::vector<int64_t> rp(n + 1, 0);
+  std::vector<int> cl;
+  cl.reserve(raw.size() / 2 + 1);
+  for (int i = 0; i < n; ++i) {
+    auto b = raw.begin() + cnt[i], e = raw.begin() + cnt[i + 1];
+    std::sort(b, e);
+    auto u = std::unique(b, e);
+    cl.insert(cl.end(), b, u);
+    rp[i + 1] = static_cast<int64_t>(cl.size());
+  }
+  *nnz = rp[n];
+  if (!rowptr || !col || !valM || !valF) return IRK_OK;   // size query
+  std::copy(rp.begin(), rp.end(), rowptr);
+  std::copy(cl.begin(), cl.end(), col);
+  std::fill(valM, valM + rp[n], 0.0);
+  std::fill(valF, valF + rp[n], 0.0);
+  if (g) std::fill(g, g + n, 0.0);
+  double bary[6][3], w[6];
+  rule(bary, w);
+  // basis values and barycentric-gradient coefficients at the rule's points
+  double phi[6][6], dl[6][6][3];
+  for (int q = 0; q < 6; ++q) {
+    const double* l = bary[q];
+    const int ea[3] = {0, 1, 2}, eb[3] = {1, 2, 0};
+    for (int k = 0; k < 6; ++k)
+      for (int i = 0; i < 3; ++i) dl[q][k][i] = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      phi[q][i] = l[i] * (2.0 * l[i] - 1.0);
+      dl[q][i][i] = 4.0 * l[i] - 1.0;
+    }
+    for (int k = 0; k < 3; ++k) {
+      int i = ea[k], j = eb[k];
+      phi[q][3 + k] = 4.0 * l[i] * l[j];
+      dl[q][3 + k][i] = 4.0 * l[j];
+      dl[q][3 + k][j] = 4.0 * l[i];
+    }
+  }
+  for (int e = 0; e < n_tri; ++e) {
+    const int32_t* t = tri6 + 6 * e;
+    Geo geo;
+    if (!geometry(xy, t, geo)) {
+      irk::set_global_error("mesh triangles must be counter-clockwise and non-degenerate");
+      return IRK_ERR_INVALID;
+    }
+    double ke = kappa ? kappa[e] : 1.0;
+    double Me[6][6], Fe[6][6];
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) {
+        double sm = 0.0, sk = 0.0;
+        for (int q = 0; q < 6; ++q) {
+          double gax = 0.0, gay = 0.0, gbx = 0.0, gby = 0.0;
+          for (int i = 0; i < 3; ++i) {
+            gax += dl[q][a][i] * geo.gx[i];
+            gay += dl[q][a][i] * geo.gy[i];
+            gbx += dl[q][b][i] * geo.gx[i];
+            gby += dl[q][b][i] * geo.gy[i];
+          }
+          sm += w[q] * phi[q][a] * phi[q][b];
+          sk += w[q] * (gax * gbx + gay * gby);
+        }
+        Me[a][b] = geo.area * sm;
+        Fe[a][b] = ke * geo.area * sk;
+      }
+    for (int a = 0; a < 6; ++a) {
+      int da = dof[t[a]];
+      if (da < 0) continue;
+      for (int b = 0; b < 6; ++b) {
         int db = dof[t[b]];
         if (db < 0) {
           if (g && ub) g[da] += Fe[a][b] * ub[t[b]];

@@ -338,6 +338,7 @@ struct Ctx {
   void* Z = nullptr;        // m * N in the AMG precision
   double* x = nullptr;      // N
   double* bv = nullptr;     // N (right-hand side)
+  int* rhs_given = nullptr; // device flag: the forward head takes bv as given (irk_solve)
   double* u = nullptr;      // n (current state)
   double* lam = nullptr;    // n (adjoint state)
   double* tmpn = nullptr;   // n

@@ -447,10 +447,26 @@ template <int S>
 __global__ void __launch_bounds__(BS)
 k_rhs_forward(int n, SellView<double> Fv, const double* __restrict__ u, const double* __restrict__ g,
               double* __restrict__ b, double* __restrict__ V0, double* __restrict__ x, GmresState* st,
-              double* __restrict__ partials, int m, int max_it, double rtol, double eta2) {
+              double* __restrict__ partials, int m, int max_it, double rtol, double eta2,
+              const int* __restrict__ given) {
   pdl_trigger();
   pdl_wait();
   double nrm = 0.0;
+  if (*given) {   // irk_solve: b was copied into place by the caller
+    for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        double t = b[int64_t(i) * n + r];
+        V0[int64_t(i) * n + r] = t;
+        x[int64_t(i) * n + r] = 0.0;
+        nrm = fma(t, t, nrm);
+      }
+    }
+    double v[1] = {nrm};
+    block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
+    if (last_block(st)) gmres_init_last(st, partials, m, max_it, rtol, eta2);
+    return;
+  }
   for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
     int sl = r >> 5, lane = r & 31;
     int64_t base = Fv.sptr[sl];
@@ -953,7 +969,7 @@ static double reorth_eta2(const Ctx& c) { return c.reorth == 1 ? -1.0 : c.reorth
 void rhs_forward_launch(Ctx& c, const double* u, cudaStream_t st) {
   IRK_DISPATCH_S(c.s, {
     launch_k(k_rhs_forward<S>, row_grid(c), BS, 0, st, c.n, view<double>(c.Fs), u, c.g, c.bv, c.V, c.x, c.st, c.partials,
-                                                 c.m, c.max_it, c.rtol, reorth_eta2(c));
+                                                 c.m, c.max_it, c.rtol, reorth_eta2(c), c.rhs_given);
   });
   CK_LAUNCH();
 }

@@ -173,3 +173,18 @@ def test_setup_rejects_bad_options_before_device_work(L, field, value):
     st = L.irk_setup(C.byref(prob), C.byref(bt), 0.1, C.byref(o), None, C.byref(out))
     assert st == 1 and not out.value
     assert L.irk_last_error(None)
+
+
+@pytest.mark.parametrize("N", [3, 10])
+def test_fem_p2_heat_matches_oracle(L, N):
+    """libirk's host P2 assembly (its own quadrature) against the oracle's."""
+    from paper_2010_11377_gb300 import problems
+    p = problems.heat_p2(N)
+    mesh = synth.structured_mesh_p2(N)
+    o = ofem.heat_problem_p2(mesh)
+    import scipy.sparse as sp
+    M = sp.csr_matrix((p["valM"], p["col"], p["rowptr"]), shape=(p["n"], p["n"]))
+    F = sp.csr_matrix((p["valF"], p["col"], p["rowptr"]), shape=(p["n"], p["n"]))
+    assert p["n"] == (2 * N - 1) ** 2
+    assert abs(M - o.M).max() <= 1e-15 * max(1.0, abs(o.M).max()) + 1e-17
+    assert abs(F - o.F).max() <= 1e-13

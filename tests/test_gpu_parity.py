@@ -222,6 +222,31 @@ def test_heat_c1_run(kind):
         assert np.linalg.norm(host(ck[q]) - refs[5 * q]) <= 1e-8 * np.linalg.norm(refs[5 * q])
 
 
+@pytest.mark.parametrize("side", ["right", "left"])
+@pytest.mark.parametrize("kind", ["J", "LD"])
+def test_p2_manufactured_solve(side, kind):
+    """irk_solve on the P2 heat matrices (the paper's runs, Section 5) for a
+    manufactured right-hand side b = A k* (random k*, Radau IIA s = 3,
+    h_t = h_x^(3/5)): k within 1e-7 of k*, FP64 AMG, iteration counts within
+    10% of the oracle's (F)GMRES with the same AMG reading on the same b."""
+    N, s_ = 12, 3
+    mesh = synth.structured_mesh_p2(N)
+    prob = ofem.heat_problem_p2(mesh)
+    A, b, _ = obt.radau_iia(s_)
+    h = (1.0 / N) ** (3.0 / (2 * s_ - 1))
+    ctx, At = oracle_ctx(prob, A, kind, h, amg_prec="f64", b=b, side=side, **AMG_OPTS)
+    kstar = synth.random_stage_block(prob.n, s_, 7)
+    rhs = oirk.apply_operator(prob.M, prob.F, A, h, kstar)
+    k = torch.empty(s_ * prob.n, dtype=torch.float64, device="cuda")
+    st = B().irk_solve(ctx, dev(rhs.ravel()), k)
+    got = host(k).reshape(s_, prob.n)
+    assert np.linalg.norm(got - kstar) <= 1e-7 * np.linalg.norm(kstar)
+    sol = oirk.IRKSolver(prob, A, b, h, kind=kind, subsolve="amg", amg_opts=oracle_amg_opts(), Atilde=At,
+                         side=side)
+    oit = sol.solve_stages(rhs).iterations
+    assert _its_close(st["iterations"], oit), (st["iterations"], oit)
+
+
 @pytest.mark.parametrize("kind", ["GSL", "LD"])
 @pytest.mark.parametrize("s", [2, 5])
 def test_left_preconditioned_steps(kind, s):
