@@ -192,3 +192,129 @@ def double_glazing_problem(mesh, eps, wind, ub):
     F, F_IB = restrict(Ffull, mesh.interior, bnodes)
     g = F_IB @ ub[bnodes]
     return Problem(M, F, g, mesh, eps=eps, kind="double_glazing")
+
+
+# ----------------------------------------------------------------------------
+# Double glazing with SUPG stabilisation and Nitsche boundary conditions (the
+# paper's discretisation of the advection-diffusion runs, Section 5)
+# ----------------------------------------------------------------------------
+
+def boundary_edges(mesh):
+    """(tri index, local vertex a, local vertex b) of every boundary edge: both
+    end nodes on the boundary and the edge on one of the four walls."""
+    out = []
+    xy, tri = mesh.xy, mesh.tri
+    lo, hi = mesh.lo, mesh.hi
+    for e in range(tri.shape[0]):
+        for a in range(3):
+            b = (a + 1) % 3
+            pa, pb = xy[tri[e, a]], xy[tri[e, b]]
+            for ax, val in ((0, lo[0]), (0, hi[0]), (1, lo[1]), (1, hi[1])):
+                if pa[ax] == val and pb[ax] == val:
+                    out.append((e, a, b))
+    return out
+
+
+def supg_parameter(area, G, w_c, eps):
+    """Per element: the streamline length h_e = 2|w_e| / sum_a |w_e . grad l_a|
+    (Tezduyar and Park), the mesh Peclet number P_e = |w_e| h_e / (2 eps) and
+    delta_e = h_e / (2|w_e|) (1 - 1/P_e) when P_e > 1, else 0 (Elman,
+    Silvester and Wathen, the reference of Section 3.2), w_e = the wind at the
+    centroid."""
+    wn = np.linalg.norm(w_c, axis=1)
+    proj = np.abs(np.einsum("ei,eai->ea", w_c, G)).sum(axis=1)
+    he = np.where(proj > 0, 2.0 * wn / np.where(proj > 0, proj, 1.0), 0.0)
+    Pe = wn * he / (2.0 * eps)
+    delta = np.where(Pe > 1.0, he / (2.0 * np.where(wn > 0, wn, 1.0)) * (1.0 - 1.0 / np.where(Pe > 0, Pe, 1.0)),
+                     0.0)
+    return delta
+
+
+def double_glazing_supg_nitsche(mesh, eps, wind, ub, gamma=10.0):
+    """All-node matrices of
+        (M + S_M) u' + (eps K + C + S + N) u = G
+    on the P1 mesh: S_M[i,j] = delta_e int phi_j (w_e . grad phi_i),
+    S[i,j] = delta_e int (w . grad phi_j)(w_e . grad phi_i) (the streamline
+    residual of the Galerkin convection, tested along the centroid wind),
+    Nitsche's symmetric terms on the boundary edges
+        N[i,j] = -eps int_e (grad phi_j . n) phi_i - eps int_e (grad phi_i . n) phi_j
+                 + (gamma eps / |e|) int_e phi_i phi_j,
+    and the load G[i] = -eps int_e (grad phi_i . n) u_B + (gamma eps / |e|) int_e u_B phi_i
+    with u_B linear along each edge from the nodal values ub.  The wind is
+    tangential on the walls, so there is no inflow term.  Every node is an
+    unknown; the stage right-hand side uses g = -G."""
+    xy, tri = mesh.xy, mesh.tri
+    nn = xy.shape[0]
+    nt = tri.shape[0]
+    area, G = element_geometry(xy, tri)
+    base = assemble(xy, tri, wind=wind)
+    p = xy[tri]
+    centroid = p.mean(axis=1)
+    w_c = wind(centroid[:, 0], centroid[:, 1])
+    delta = supg_parameter(area, G, w_c, eps)
+    xi, eta, wq = _duffy_rule(3)
+    lam = np.stack([1.0 - xi - eta, xi, eta], axis=1)
+    X = np.einsum("qa,eai->eqi", lam, p)
+    W = wind(X[..., 0], X[..., 1])                      # (nt, nq, 2)
+    Wint = 2.0 * area[:, None] * np.einsum("q,eqi->ei", wq, W)   # int_T w
+    wcg = np.einsum("ei,eai->ea", w_c, G)               # w_e . grad l_i
+    wig = np.einsum("ei,ebi->eb", Wint, G)              # (int_T w) . grad l_j
+    Se = delta[:, None, None] * wcg[:, :, None] * wig[:, None, :]
+    SMe = delta[:, None, None] * wcg[:, :, None] * (area / 3.0)[:, None, None] * np.ones((1, 1, 3))
+    rows = np.repeat(tri, 3, axis=1).ravel()
+    cols = np.tile(tri, (1, 3)).ravel()
+    S = sp.csr_matrix((Se.ravel(), (rows, cols)), shape=(nn, nn))
+    SM = sp.csr_matrix((SMe.ravel(), (rows, cols)), shape=(nn, nn))
+    nr, nc, nv = [], [], []
+    load = np.zeros(nn)
+    for (e, a, b) in boundary_edges(mesh):
+        ia, ib = tri[e, a], tri[e, b]
+        t = xy[ib] - xy[ia]
+        L = np.hypot(t[0], t[1])
+        n = np.array([t[1], -t[0]]) / L             # outward for counter-clockwise triangles
+        gn = G[e] @ n                               # grad l_k . n, k = 0..2
+        on = {ia: None, ib: None}
+        for k in range(3):
+            for (m, i_node) in ((0, ia), (1, ib)):
+                # -eps int_e (grad phi_k . n) phi_i  and its transpose
+                nr.append(i_node); nc.append(tri[e, k]); nv.append(-eps * gn[k] * L / 2.0)
+                nr.append(tri[e, k]); nc.append(i_node); nv.append(-eps * gn[k] * L / 2.0)
+        for i_node in (ia, ib):
+            for j_node in (ia, ib):
+                nr.append(i_node); nc.append(j_node)
+                nv.append(gamma * eps / L * L / 6.0 * (2.0 if i_node == j_node else 1.0))
+        ga, gb = ub[ia], ub[ib]
+        for k in range(3):
+            load[tri[e, k]] += -eps * gn[k] * L * (ga + gb) / 2.0
+        load[ia] += gamma * eps / L * L / 6.0 * (2.0 * ga + gb)
+        load[ib] += gamma * eps / L * L / 6.0 * (2.0 * gb + ga)
+    Nmat = sp.csr_matrix((np.array(nv), (np.array(nr), np.array(nc))), shape=(nn, nn))
+    M = (base["M"] + SM).tocsr()
+    F = (eps * base["K"] + base["C"] + S + Nmat).tocsr()
+    M.sum_duplicates()
+    F.sum_duplicates()
+    M.sort_indices()
+    F.sort_indices()
+    return Problem(M, F, -load, mesh, eps=eps, kind="double_glazing_supg")
+
+
+def supg_load(mesh, eps, wind, f):
+    """int f phi_i + delta_e int f (w_e . grad phi_i) for a source f(x, y)
+    (tests only: the consistency pins of the stabilised discretisation).
+    Collapsed 4x4 Gauss (exact to degree 7)."""
+    xy, tri = mesh.xy, mesh.tri
+    area, G = element_geometry(xy, tri)
+    p = xy[tri]
+    centroid = p.mean(axis=1)
+    w_c = wind(centroid[:, 0], centroid[:, 1])
+    delta = supg_parameter(area, G, w_c, eps)
+    xi, eta, wq = _duffy_rule(4)
+    lam = np.stack([1.0 - xi - eta, xi, eta], axis=1)
+    X = np.einsum("qa,eai->eqi", lam, p)
+    fq = f(X[..., 0], X[..., 1])                          # (nt, nq)
+    wcg = np.einsum("ei,eai->ea", w_c, G)
+    le = 2.0 * area[:, None] * (np.einsum("q,eq,qa->ea", wq, fq, lam)
+                                + delta[:, None] * wcg * np.einsum("q,eq->e", wq, fq)[:, None])
+    out = np.zeros(xy.shape[0])
+    np.add.at(out, tri.ravel(), le.ravel())
+    return out

@@ -131,3 +131,45 @@ def test_p2_reproduces_quadratics():
     assert np.abs(uI - u[mesh.interior]).max() <= 1e-12
     assert abs(mats["M"].sum() - 1.0) <= 1e-14
     assert np.abs(mats["K"] @ np.ones(mesh.n_nodes)).max() <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# double glazing with SUPG and Nitsche boundary conditions (Section 5)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("eps", [0.04, 0.005])
+def test_supg_nitsche_reproduces_linear_solutions(eps):
+    """The stabilised discretisation is consistent, so a linear exact solution
+    is reproduced exactly: steady -eps Lap u + w.grad u = f (f = w.grad u,
+    Dirichlet data u through Nitsche's terms), and the semi-discrete
+    (M + S_M) u' + F u = G for u = t phi at t = 1 (source phi + w.grad phi).
+    Pins every term: Galerkin, streamline, SUPG mass, Nitsche matrix and load."""
+    import scipy.sparse.linalg as spla
+    mesh = synth.structured_mesh(12, "box")
+    wind = synth.double_glazing_wind
+    bx, cy = 0.7, -0.4
+    phi = lambda x, y: 0.3 + bx * x + cy * y
+    ub = phi(mesh.xy[:, 0], mesh.xy[:, 1])
+    P = fem.double_glazing_supg_nitsche(mesh, eps, wind, ub)
+    area, G = fem.element_geometry(mesh.xy, mesh.tri)
+    wc = wind(*mesh.xy[mesh.tri].mean(axis=1).T)
+    assert fem.supg_parameter(area, G, wc, eps).max() > 0.0     # stabilisation active
+    f = lambda x, y: wind(x, y) @ np.array([bx, cy])
+    uh = spla.spsolve(P.F.tocsc(), fem.supg_load(mesh, eps, wind, f) - P.g)
+    assert np.abs(uh - ub).max() <= 1e-12
+    f2 = lambda x, y: phi(x, y) + wind(x, y) @ np.array([bx, cy])
+    res = P.M @ ub + P.F @ ub - (fem.supg_load(mesh, eps, wind, f2) - P.g)
+    assert np.abs(res).max() <= 1e-13
+    assert P.M.shape[0] == 13 * 13     # every node is an unknown
+
+
+def test_nitsche_laplace_without_wind():
+    """w = 0: no stabilisation; Nitsche's Laplace problem still reproduces a
+    linear solution, and the matrix is symmetric."""
+    import scipy.sparse.linalg as spla
+    mesh = synth.structured_mesh(8, "box")
+    zero = lambda x, y: np.zeros(np.broadcast(x, y).shape + (2,))
+    ub = 1.0 + 2.0 * mesh.xy[:, 0] - mesh.xy[:, 1]
+    P = fem.double_glazing_supg_nitsche(mesh, 0.1, zero, ub)
+    assert abs(P.F - P.F.T).max() <= 1e-15
+    uh = spla.spsolve(P.F.tocsc(), -P.g)
+    assert np.abs(uh - ub).max() <= 1e-12
