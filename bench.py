@@ -397,7 +397,10 @@ def run_sweep(args):
       htlr  as ht with FP64 AMG, left- and right-preconditioned (stop on the preconditioned /
           the true residual respectively)
       t5  P2 heat, N in {8..128}, Radau IIA s = 2..7, h_t = h_x^(3/(2s-1)), manufactured
-          b = A k*, rtol 1e-8, J / GSL / DU / LD (the setting of the paper's Table 5)"""
+          b = A k*, rtol 1e-8, J / GSL / DU / LD (the setting of the paper's Table 5)
+      t12 SUPG + Nitsche double glazing, h_x^-1 in {64, 128}, eps in {0.04, 0.005}, s = 2..7,
+          h_t = h_x^(2/(2s-1)), manufactured b, left GMRES, FP64 AMG with Chebyshev on
+          [0.3, 1], GSL / LD (Table 12)"""
     import numpy as np
     import torch
     import synth
@@ -481,6 +484,34 @@ def run_sweep(args):
                                       "ms": round(st["ms"], 3), "resid": st["resid"], "err_vs_kstar": err}),
                           flush=True)
                     ctx.close()
+    elif args.sweep == "t12":
+        # the setting of the paper's double-glazing table: SUPG + Nitsche P1, h_x = 2/N,
+        # h_t = h_x^(2/(2s-1)), manufactured b = A k*, left-preconditioned GMRES, rtol 1e-8
+        for s in (2, 3, 4, 5, 6, 7):
+            A, b, c = B.irk_butcher_table("radau_iia", s)
+            for hinv in (64, 128):
+                for eps in (0.04, 0.005):
+                    p = problems.double_glazing_supg(2 * hinv, eps)
+                    h = (1.0 / hinv) ** (2.0 / (2 * s - 1))
+                    kstar = torch.tensor(synth.random_stage_block(p["n"], s, 2000 + hinv).ravel(), device="cuda")
+                    for kind in ("GSL", "LD"):
+                        # Chebyshev interval [0.3, 1]: on these advection-dominated SUPG
+                        # blocks the default [0.1, 1] polynomial amplifies the complex
+                        # eigenvalues near the low end and the V-cycle diverges
+                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", cheb_lo=0.3)
+                        ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o,
+                                          g=p["g"])
+                        rhs = torch.empty_like(kstar)
+                        B.irk_apply_operator(ctx, kstar, rhs)
+                        k = torch.empty_like(kstar)
+                        B.irk_solve(ctx, rhs, k)
+                        st = B.irk_solve(ctx, rhs, k)
+                        err = float((k - kstar).norm() / kstar.norm())
+                        print(json.dumps({"sweep": "t12", "problem": "double_glazing_supg", "hx_inv": hinv,
+                                          "n": p["n"], "s": s, "dof": s * p["n"], "h_t": h, "eps": eps,
+                                          "precond": kind, "its": st["iterations"], "ms": round(st["ms"], 3),
+                                          "resid": st["resid"], "err_vs_kstar": err}), flush=True)
+                        ctx.close()
     elif args.sweep == "htlr":
         p = problems.heat(128)
         u0 = synth.heat_u0(p["mesh"])
@@ -604,7 +635,7 @@ def main():
     ap.add_argument("--kernel-j", type=int, default=22, help="Gram-Schmidt basis index for --kernel")
     ap.add_argument("--kernel-warm", type=int, default=3)
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5"],
+    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t12"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--launch-list", action="store_true",

@@ -183,6 +183,26 @@ irk_status irk_fem_assemble_p2(int32_t n_nodes, const double* xy, int32_t n_tri,
                                const int32_t* dof, int32_t n, const double* kappa, const double* ub, int64_t* nnz,
                                int64_t* rowptr, int32_t* col, double* valM, double* valF, double* g);
 
+/* Double glazing with SUPG stabilisation and symmetric Nitsche boundary
+ * conditions, the discretisation of the paper's advection-diffusion runs
+ * (Section 5); every node is an unknown (n = n_nodes):
+ *   M = M_gal + S_M, S_M[i,j] = delta_e (w_e . grad l_i) |T|/3
+ *   F = eps K + C + S + N, S[i,j] = delta_e (w_e . grad l_i) (int_T w) . grad l_j
+ *   N: -eps int_e (grad phi_j . n) phi_i - eps int_e (grad phi_i . n) phi_j
+ *      + (gamma eps/|e|) int_e phi_i phi_j on every edge of only one triangle
+ *   g = -(-eps int_e (grad phi_i . n) u_B + (gamma eps/|e|) int_e u_B phi_i)
+ * delta_e = h_e/(2|w_e|)(1 - 1/P_e) when the Peclet number P_e = |w_e| h_e/(2 eps)
+ * exceeds 1, else 0, with h_e = 2|w_e| / sum_a |w_e . grad l_a|.  wind: n_tri*6*2
+ * values at irk_fem_quad_points; wind_c: n_tri*2 values at the centroids (the
+ * mean of the three vertices); ub: n_nodes boundary values (u_B is linear
+ * along each edge), NULL = 0; gamma > 0 the Nitsche penalty.  The wind must be
+ * tangential on the boundary (no inflow term).  Size query and outputs as
+ * irk_fem_assemble. */
+irk_status irk_fem_assemble_supg(int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri, double eps,
+                                 const double* wind, const double* wind_c, const double* ub, double gamma,
+                                 int64_t* nnz, int64_t* rowptr, int32_t* col, double* valM, double* valF,
+                                 double* g);
+
 /* ------------------------------------------------------------------------- *
  * Solver context.                                                            *
  * ------------------------------------------------------------------------- */

@@ -134,6 +134,28 @@ def irk_fem_assemble_p2(xy, tri6, dof, n, kappa=None, ub=None):
     return rowptr, col, valM, valF, g
 
 
+def irk_fem_assemble_supg(xy, tri, eps, wind, wind_c, ub=None, gamma=10.0):
+    """All-node CSR (rowptr, col, valM, valF) and lift g of the SUPG / Nitsche
+    double-glazing discretisation."""
+    L = lib()
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    wind = np.ascontiguousarray(wind, dtype=np.float64)
+    wind_c = np.ascontiguousarray(wind_c, dtype=np.float64)
+    ub = None if ub is None else np.ascontiguousarray(ub, dtype=np.float64)
+    n = xy.shape[0]
+    nnz = C.c_int64(0)
+    args = (n, _dp(xy), tri.shape[0], _ip(tri), float(eps), _dp(wind), _dp(wind_c), _dp(ub), float(gamma))
+    check(L.irk_fem_assemble_supg(*args, C.byref(nnz), None, None, None, None, None))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    valM = np.zeros(nnz.value)
+    valF = np.zeros(nnz.value)
+    g = np.zeros(n)
+    check(L.irk_fem_assemble_supg(*args, C.byref(nnz), _lp(rowptr), _ip(col), _dp(valM), _dp(valF), _dp(g)))
+    return rowptr, col, valM, valF, g
+
+
 # ---------------------------------------------------------------------------
 # context
 # ---------------------------------------------------------------------------

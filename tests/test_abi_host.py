@@ -188,3 +188,21 @@ def test_fem_p2_heat_matches_oracle(L, N):
     assert p["n"] == (2 * N - 1) ** 2
     assert abs(M - o.M).max() <= 1e-15 * max(1.0, abs(o.M).max()) + 1e-17
     assert abs(F - o.F).max() <= 1e-13
+
+
+@pytest.mark.parametrize("eps", [0.04, 0.005])
+def test_fem_supg_nitsche_matches_oracle(L, eps):
+    """libirk's SUPG / Nitsche assembly (degree-4 rule, edge-count boundary
+    detection) against the oracle's (collapsed Gauss, wall test)."""
+    from paper_2010_11377_gb300 import problems
+    import scipy.sparse as sp
+    N = 14
+    p = problems.double_glazing_supg(N, eps)
+    mesh = synth.structured_mesh(N, "box")
+    o = ofem.double_glazing_supg_nitsche(mesh, eps, synth.double_glazing_wind, synth.double_glazing_boundary(mesh))
+    M = sp.csr_matrix((p["valM"], p["col"], p["rowptr"]), shape=(p["n"], p["n"]))
+    F = sp.csr_matrix((p["valF"], p["col"], p["rowptr"]), shape=(p["n"], p["n"]))
+    assert p["n"] == (N + 1) ** 2
+    assert abs(M - o.M).max() <= 1e-15
+    assert abs(F - o.F).max() <= 1e-14
+    assert np.abs(p["g"] - o.g).max() <= 1e-14

@@ -222,6 +222,32 @@ def test_heat_c1_run(kind):
         assert np.linalg.norm(host(ck[q]) - refs[5 * q]) <= 1e-8 * np.linalg.norm(refs[5 * q])
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["GSL", "LD"])
+def test_supg_nitsche_steps(prec, kind):
+    """Double glazing with SUPG and Nitsche terms (nonsymmetric M and F, every
+    node an unknown): 3 steps within 1e-8 of the oracle's exact stage solves,
+    iteration counts within 10% of the oracle's FGMRES on the same matrices."""
+    N, eps = 24, 0.005
+    mesh = synth.structured_mesh(N, "box")
+    prob = ofem.double_glazing_supg_nitsche(mesh, eps, synth.double_glazing_wind, synth.double_glazing_boundary(mesh))
+    A, b, _ = obt.radau_iia(3)
+    h = 0.05
+    ctx, At = oracle_ctx(prob, A, kind, h, amg_prec=prec, b=b, **AMG_OPTS)
+    u0 = synth.double_glazing_boundary(mesh)
+    refs, _ = oirk.IRKSolver(prob, A, b, h, kind=None).run(u0, 3, direct=True)
+    amg_sol = oirk.IRKSolver(prob, A, b, h, kind=kind, subsolve="amg", amg_opts=oracle_amg_opts(), Atilde=At)
+    u = dev(u0)
+    for t in range(3):
+        out = torch.empty_like(u)
+        st = B().irk_step(ctx, u, out)
+        err = np.linalg.norm(host(out) - refs[t + 1]) / np.linalg.norm(refs[t + 1])
+        assert err < 1e-8, (t, err)
+        if prec == "f64":
+            assert _its_close(st["iterations"], amg_sol.step(refs[t]).iterations)
+        u = out
+
+
 @pytest.mark.parametrize("side", ["right", "left"])
 @pytest.mark.parametrize("kind", ["J", "LD"])
 def test_p2_manufactured_solve(side, kind):
