@@ -109,6 +109,8 @@ typedef struct {
                             Left preconditioning needs a fixed linear P^{-1}: use FP64 AMG for
                             rtol below the AMG precision.  Forward solves only: the adjoint
                             entry points and batches reject side = 1 */
+  int32_t p_smooth;      /* damped-Jacobi steps smoothing the tentative prolongator,
+                            P = (I - omega D^{-1} A)^p_smooth P_t, 1..3 (default 2) */
 } irk_options;
 
 typedef struct {
@@ -146,7 +148,8 @@ irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, 
 
 /* Fill *opt with the defaults: P_LD, FP32 AMG, Chebyshev degree 4 on [0.1, 1],
  * V(1,1), theta 0.08, coarse_max 2048, 12 levels, FGMRES(30), rtol 1e-10,
- * max_it 1000, selective reorthogonalisation (reorth_eta 0.1). */
+ * max_it 1000, selective reorthogonalisation (reorth_eta 0.1), right preconditioning,
+ * two prolongator smoothing steps. */
 void irk_default_options(irk_options* opt);
 
 /* ------------------------------------------------------------------------- *

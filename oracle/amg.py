@@ -19,8 +19,9 @@ reading fixed in the design notes, step by step:
              every other node joins the aggregate of its phase-1 strong
              neighbour of largest priority (phase 2).  Aggregates are
              numbered by increasing root index.
-  P          tentative piecewise constant P_t (entries 1), smoothed once:
-             P = (I - omega D^{-1} A) P_t, omega = 4 / (3 rho),
+  P          tentative piecewise constant P_t (entries 1), smoothed by
+             p_smooth damped-Jacobi steps (default 2):
+             P = (I - omega D^{-1} A)^p_smooth P_t, omega = 4 / (3 rho),
              rho = max_i sum_j |a_ij| / |a_ii|.
   coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max (2048) or
              coarsening stalls (the next level would keep more than 90% of the
@@ -136,14 +137,17 @@ def aggregate(G: sp.csr_matrix, level: int):
     return agg, root
 
 
-def smoothed_prolongator(A: sp.csr_matrix, agg: np.ndarray, nc: int):
+def smoothed_prolongator(A: sp.csr_matrix, agg: np.ndarray, nc: int, steps: int = 2):
+    """P = (I - omega D^{-1} A)^steps P_t, one damped-Jacobi step at a time."""
     n = A.shape[0]
     Pt = sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, nc))
     diag = A.diagonal()
     rho = np.max(np.asarray(abs(A).sum(axis=1)).ravel() / np.abs(diag))
     omega = 4.0 / (3.0 * rho)
     Dinv = sp.diags(1.0 / diag)
-    P = (Pt - omega * (Dinv @ (A @ Pt))).tocsr()
+    P = Pt
+    for _ in range(steps):
+        P = (P - omega * (Dinv @ (A @ P))).tocsr()
     P.sort_indices()
     return P, omega
 
@@ -165,7 +169,7 @@ class Hierarchy:
 
     def __init__(self, A, theta=0.08, coarse_max=2048, max_levels=12,
                  nu_pre=1, nu_post=1, smoother="chebyshev", cheb_degree=4,
-                 cheb_lo=0.1):
+                 cheb_lo=0.1, p_smooth=2):
         self.theta = theta
         self.nu_pre = nu_pre
         self.nu_post = nu_post
@@ -191,7 +195,7 @@ class Hierarchy:
             nc = int(agg.max()) + 1
             if 10 * nc > 9 * lev.n:
                 break
-            P, _ = smoothed_prolongator(lev.A, agg, nc)
+            P, _ = smoothed_prolongator(lev.A, agg, nc, p_smooth)
             lev.P = P
             lev.R = P.T.tocsr()
             lev.agg = agg

@@ -372,6 +372,29 @@ static T rd(const T* d, cudaStream_t st) {
 static inline unsigned nb(int64_t n, int bs = 256) { return nblk(n, bs); }
 
 // one coarsening step: fills lev.agg, lev.P (as CSR) and the coarse CSR Ac
+// One more damped-Jacobi step on the prolongator, on the pattern of A P:
+// out[r,J] = P[r,J] - omega ((1/a_rr) (A P)[r,J])  (P[r,J] = 0 off its pattern).
+// The pattern of A P contains that of P (A has its diagonal); a P entry
+// missing from it sets *bad.
+__global__ void k_psmooth_merge(int n, const int* __restrict__ prp, const int* __restrict__ pcol,
+                                const double* __restrict__ pval, const int* __restrict__ arp,
+                                const int* __restrict__ acol, const double* __restrict__ aval,
+                                const double* __restrict__ diag, double omega, double* __restrict__ out,
+                                int* __restrict__ bad) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int q = prp[r];
+  const int qe = prp[r + 1];
+  const double dinv = 1.0 / diag[r];
+  for (int k = arp[r]; k < arp[r + 1]; ++k) {
+    double pv = 0.0;
+    if (q < qe && pcol[q] == acol[k]) pv = pval[q++];
+    else if (q < qe && pcol[q] < acol[k]) atomicOr(bad, 1);
+    out[k] = __dsub_rn(pv, __dmul_rn(omega, __dmul_rn(dinv, aval[k])));
+  }
+  if (q != qe) atomicOr(bad, 1);
+}
+
 static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R, CsrD& Ac, DevPool& pool,
                     cudaStream_t st) {
   const CsrD& A = lev.A;
@@ -457,6 +480,26 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
   P.val = pool.get<double>(P.nnz);
   k_prolong_fill<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, lev.agg, omega, P.rowptr, P.col,
                                         P.val);
+  // further Jacobi steps: P <- P - omega D^{-1} (A P)
+  for (int q = 1; q < p.p_smooth; ++q) {
+    CK_LAUNCH();
+    CsrD AP1;
+    csr_spgemm(A, P, AP1, pool, st);
+    double* v2 = pool.get<double>(AP1.nnz > 0 ? AP1.nnz : 1);
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    k_psmooth_merge<<<nb(n), 256, 0, st>>>(n, P.rowptr, P.col, P.val, AP1.rowptr, AP1.col, AP1.val, diag, omega,
+                                           v2, bad);
+    CK_LAUNCH();
+    if (rd(bad, st)) fail(IRK_ERR_INVALID, "prolongator pattern not contained in that of A P");
+    pool.release(P.rowptr);
+    pool.release(P.col);
+    pool.release(P.val);
+    pool.release(AP1.val);
+    P.rowptr = AP1.rowptr;
+    P.col = AP1.col;
+    P.val = v2;
+    P.nnz = AP1.nnz;
+  }
   CK_LAUNCH();
   csr_transpose(P, R, pool, st);
   CsrD AP;

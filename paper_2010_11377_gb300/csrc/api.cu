@@ -408,6 +408,7 @@ void irk_default_options(irk_options* o) {
   o->reorth = 0;
   o->reorth_eta = 0.1;
   o->side = 0;
+  o->p_smooth = 2;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -447,6 +448,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (!(o.reorth_eta >= 0.0 && o.reorth_eta < 1.0) || o.reorth < 0 || o.reorth > 1)
     return set_err(nullptr, IRK_ERR_INVALID, "reorth must be 0 or 1 and 0 <= reorth_eta < 1");
   if (o.side != 0 && o.side != 1) return set_err(nullptr, IRK_ERR_INVALID, "side must be 0 (right) or 1 (left)");
+  if (o.p_smooth < 1 || o.p_smooth > 3) return set_err(nullptr, IRK_ERR_INVALID, "p_smooth must be 1..3");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
     return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..2048");
   const irk_csr& M = prob->M;
@@ -488,6 +490,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     c.amg.smoother = o.smoother;
     c.amg.cheb_degree = o.cheb_degree;
     c.amg.cheb_lo = o.cheb_lo;
+    c.amg.p_smooth = o.p_smooth;
     c.amg.nu_pre = o.nu_pre;
     c.amg.nu_post = o.nu_post;
     c.amg.amg_prec = o.amg_prec;

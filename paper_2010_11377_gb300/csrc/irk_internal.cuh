@@ -210,6 +210,7 @@ struct AmgParams {
   double cheb_lo = 0.1;
   int nu_pre = 1, nu_post = 1;
   int amg_prec = 32;
+  int p_smooth = 2;        // damped-Jacobi steps on the tentative prolongator
 };
 
 // Chebyshev step coefficients: step i updates d_i = alpha_i d_{i-1} + beta_i D^{-1}(b - A x_i)

@@ -138,3 +138,24 @@ def test_vcycle_nonsymmetric_block():
     for _ in range(10):
         x = x + H.vcycle(b - Bk @ x)
     assert np.linalg.norm(b - Bk @ x) < 1e-2 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("steps", [1, 2])
+def test_prolongator_is_jacobi_power(steps):
+    """P = (I - omega D^{-1} A)^steps P_t against the dense matrix power, and
+    the constant vector on the aggregates stays in range: P 1_c = S^steps 1."""
+    mesh = synth.structured_mesh(9)
+    prob = fem.heat_problem(mesh)
+    A = (prob.M + 0.01 * prob.F).tocsr()
+    G = amg.strength_graph(A, 0.08)
+    agg, _ = amg.aggregate(G, 0)
+    nc = int(agg.max()) + 1
+    P, omega = amg.smoothed_prolongator(A, agg, nc, steps)
+    Ad = A.toarray()
+    S = np.eye(A.shape[0]) - omega * Ad / np.diag(Ad)[:, None]
+    Pt = np.zeros((A.shape[0], nc))
+    Pt[np.arange(A.shape[0]), agg] = 1.0
+    ref = np.linalg.matrix_power(S, steps) @ Pt
+    assert np.abs(P.toarray() - ref).max() <= 1e-14
+    rho = np.max(np.abs(Ad).sum(axis=1) / np.abs(np.diag(Ad)))
+    assert omega == 4.0 / (3.0 * rho)
