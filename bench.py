@@ -335,7 +335,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded P1 heat problem; u0 = sin(pi x) sin(pi y))",
         "config": {"workload": name, "grid": f"{N}x{N}", "n_per_stage": n, "stages": s, "method": "Radau IIA",
-                   "h_t": h, "precond": f"P_{kind}", "amg": prec + " V-cycle (Chebyshev 4, V(1,1), coarsest <= 2048 rows)",
+                   "h_t": h, "precond": f"P_{kind}", "amg": prec + " SA V-cycle (prolongator smoothed twice, Chebyshev 4, V(1,1), coarsest <= 2048 rows)",
                    "krylov": "FGMRES(30) rtol 1e-10", "parallelism": f"replicas x{world}",
                    "l2": "working set > L2 (Krylov bases 1.3 GB); no flush"},
         "iterations_per_step": its, "resid": st["resid"], "setup_s": setup_s,
@@ -390,7 +390,8 @@ def run_sweep(args):
     FGMRES(30), FP32 AMG unless stated; `--sweep-steps` timed steps after one
     untimed step, times per step from CUDA events):
       c2  heat N in {256, 512, 1024}, Radau IIA s in {3, 5, 7}, h_t = 1/64, J / GSL / GSL_OPT / DU / LD
-      c3  double glazing N in {256, 512, 1024}, s = 2..7, h_t = 0.01, GSL / LD
+      c3  double glazing N in {256, 512, 1024}, s = 2..7, h_t = 0.01, GSL / LD (one
+          prolongator smoothing step: a second costs time without saving iterations here)
       c4  N = 1024, s = 5, LD: AMG in FP64 / FP32 / BF16-finest, heat and double glazing
       ht  heat N = 128, s in {2, 7}, h_t in {0.05, 0.1, 0.5, 1, 5}, GSL / LD, rtol 1e-8
       lob heat N in {256, 1024}, Lobatto IIIC s in {2, 3, 4, 5}, h_t = 1/64, J / GSL / DU / LD
@@ -410,9 +411,9 @@ def run_sweep(args):
     from paper_2010_11377_gb300 import problems
     steps = args.sweep_steps
 
-    def run(p, s, h, kind, u0, prec="f32", rtol=1e-10, tag="", method="radau_iia", side="right"):
+    def run(p, s, h, kind, u0, prec="f32", rtol=1e-10, tag="", method="radau_iia", side="right", p_smooth=2):
         A, b, c = B.irk_butcher_table(method, s)
-        o = B.irk_default_options(kind=kind, amg_prec=prec, rtol=rtol, side=side)
+        o = B.irk_default_options(kind=kind, amg_prec=prec, rtol=rtol, side=side, p_smooth=p_smooth)
         t0 = time.perf_counter()
         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o, g=p["g"])
         setup = time.perf_counter() - t0
@@ -425,7 +426,8 @@ def run_sweep(args):
         ms = st["ms"] / steps
         print(json.dumps({"sweep": tag, "problem": p["kind"], "method": method, "side": side, "N": p["N"], "n": p["n"],
                           "s": s, "h_t": h,
-                          "precond": kind, "amg": prec, "rtol": rtol, "its_per_step": st["iterations"] / steps,
+                          "precond": kind, "amg": prec, "p_smooth": p_smooth, "rtol": rtol,
+                          "its_per_step": st["iterations"] / steps,
                           "max_step_its": st["max_step_iterations"], "ms_per_step": round(ms, 3),
                           "value": s * p["n"] / (ms * 1e-3), "resid": st["resid"], "setup_s": round(setup, 3),
                           "amg_rows": rows}), flush=True)
@@ -444,7 +446,7 @@ def run_sweep(args):
             u0 = np.zeros(p["n"])
             for s in (2, 3, 4, 5, 6, 7):
                 for kind in ("GSL", "LD"):
-                    run(p, s, 0.01, kind, u0, tag="c3")
+                    run(p, s, 0.01, kind, u0, tag="c3", p_smooth=1)
     elif args.sweep == "c4":
         p = problems.heat(1024)
         u0 = synth.heat_u0(p["mesh"])
@@ -453,7 +455,7 @@ def run_sweep(args):
         p = problems.double_glazing(1024)
         u0 = np.zeros(p["n"])
         for prec in ("f64", "f32", "bf16"):
-            run(p, 5, 0.01, "LD", u0, prec, tag="c4")
+            run(p, 5, 0.01, "LD", u0, prec, tag="c4", p_smooth=1)
     elif args.sweep == "lob":
         for N in (256, 1024):
             p = problems.heat(N)

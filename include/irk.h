@@ -110,7 +110,8 @@ typedef struct {
                             rtol below the AMG precision.  Forward solves only: the adjoint
                             entry points and batches reject side = 1 */
   int32_t p_smooth;      /* damped-Jacobi steps smoothing the tentative prolongator,
-                            P = (I - omega D^{-1} A)^p_smooth P_t, 1..3 (default 2) */
+                            P = (I - omega D^{-1} A)^p_smooth P_t, 1 or 2 (default 2); the
+                            second step only on levels with at most 80 entries per row */
 } irk_options;
 
 typedef struct {

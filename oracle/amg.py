@@ -20,8 +20,9 @@ reading fixed in the design notes, step by step:
              neighbour of largest priority (phase 2).  Aggregates are
              numbered by increasing root index.
   P          tentative piecewise constant P_t (entries 1), smoothed by
-             p_smooth damped-Jacobi steps (default 2):
-             P = (I - omega D^{-1} A)^p_smooth P_t, omega = 4 / (3 rho),
+             p_smooth damped-Jacobi steps (default 2) on levels whose matrix
+             has at most 80 entries per row on average, one step on denser
+             levels: P = (I - omega D^{-1} A)^steps P_t, omega = 4 / (3 rho),
              rho = max_i sum_j |a_ij| / |a_ii|.
   coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max (2048) or
              coarsening stalls (the next level would keep more than 90% of the
@@ -195,7 +196,10 @@ class Hierarchy:
             nc = int(agg.max()) + 1
             if 10 * nc > 9 * lev.n:
                 break
-            P, _ = smoothed_prolongator(lev.A, agg, nc, p_smooth)
+            # the extra smoothing step widens P and the coarse operator; it is
+            # taken only on levels with at most 80 entries per row on average
+            steps = p_smooth if lev.A.nnz <= 80 * lev.n else 1
+            P, _ = smoothed_prolongator(lev.A, agg, nc, steps)
             lev.P = P
             lev.R = P.T.tocsr()
             lev.agg = agg

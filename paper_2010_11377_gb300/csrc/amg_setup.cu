@@ -480,8 +480,10 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
   P.val = pool.get<double>(P.nnz);
   k_prolong_fill<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, lev.agg, omega, P.rowptr, P.col,
                                         P.val);
-  // further Jacobi steps: P <- P - omega D^{-1} (A P)
-  for (int q = 1; q < p.p_smooth; ++q) {
+  // further Jacobi steps: P <- P - omega D^{-1} (A P), on levels with at most
+  // 80 entries per row on average (the step widens P and the coarse operator)
+  const int steps = (A.nnz <= 80LL * n) ? p.p_smooth : 1;
+  for (int q = 1; q < steps; ++q) {
     CK_LAUNCH();
     CsrD AP1;
     csr_spgemm(A, P, AP1, pool, st);

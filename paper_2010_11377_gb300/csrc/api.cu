@@ -448,7 +448,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (!(o.reorth_eta >= 0.0 && o.reorth_eta < 1.0) || o.reorth < 0 || o.reorth > 1)
     return set_err(nullptr, IRK_ERR_INVALID, "reorth must be 0 or 1 and 0 <= reorth_eta < 1");
   if (o.side != 0 && o.side != 1) return set_err(nullptr, IRK_ERR_INVALID, "side must be 0 (right) or 1 (left)");
-  if (o.p_smooth < 1 || o.p_smooth > 3) return set_err(nullptr, IRK_ERR_INVALID, "p_smooth must be 1..3");
+  if (o.p_smooth < 1 || o.p_smooth > 2) return set_err(nullptr, IRK_ERR_INVALID, "p_smooth must be 1 or 2");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
     return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..2048");
   const irk_csr& M = prob->M;
