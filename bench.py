@@ -401,7 +401,7 @@ def run_sweep(args):
           b = A k*, rtol 1e-8, J / GSL / DU / LD (the setting of the paper's Table 5)
       t12 SUPG + Nitsche double glazing, h_x^-1 in {64, 128}, eps in {0.04, 0.005}, s = 2..7,
           h_t = h_x^(2/(2s-1)), manufactured b, left GMRES, FP64 AMG with Chebyshev on
-          [0.3, 1], GSL / LD (Table 12)"""
+          [0.3, 1] and one prolongator smoothing step, GSL / LD (Table 12)"""
     import numpy as np
     import torch
     import synth
@@ -500,7 +500,8 @@ def run_sweep(args):
                         # Chebyshev interval [0.3, 1]: on these advection-dominated SUPG
                         # blocks the default [0.1, 1] polynomial amplifies the complex
                         # eigenvalues near the low end and the V-cycle diverges
-                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", cheb_lo=0.3)
+                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", cheb_lo=0.3,
+                                                  p_smooth=1)
                         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o,
                                           g=p["g"])
                         rhs = torch.empty_like(kstar)
