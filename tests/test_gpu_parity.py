@@ -97,14 +97,15 @@ def test_operator_parity(s):
 
 
 @pytest.mark.parametrize("which", ["heat", "dg"])
-def test_aggregates_and_galerkin_parity(which):
+@pytest.mark.parametrize("p_smooth", [1, 2])
+def test_aggregates_and_galerkin_parity(which, p_smooth):
     mesh, prob = heat(57) if which == "heat" else dg(57)
     A, _, _ = obt.radau_iia(3)
     h = 1 / 64 if which == "heat" else 0.01
-    ctx, At = oracle_ctx(prob, A, "LD", h, **AMG_OPTS)
+    ctx, At = oracle_ctx(prob, A, "LD", h, p_smooth=p_smooth, **AMG_OPTS)
     for stage in range(3):
         Bk = (prob.M + (h * At[stage, stage]) * prob.F).tocsr()
-        H = oamg.Hierarchy(Bk, **oracle_amg_opts())
+        H = oamg.Hierarchy(Bk, p_smooth=p_smooth, **oracle_amg_opts())
         rows, nnz = B().irk_amg_info(ctx, stage)
         assert rows[0] == prob.n
         # level 0: bit-identical block, identical aggregates
