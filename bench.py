@@ -315,12 +315,14 @@ def run_ours(args):
 
     name = args.workload
     N, s, h, kind, prec = WORKLOADS[name]
+    free0 = torch.cuda.mem_get_info()[0]
     ctx, prob, setup_s = build_context(name)
     u = torch.tensor(synth.heat_u0(prob["mesh"]), dtype=torch.float64, device="cuda")
     n = prob["n"]
     dev_index = torch.cuda.current_device()
     with ClockSampler(dev_index) as clk:
         ms, st, launches, uN = timed_steps(ctx, u, args.steps, args.warmup, dist)
+    device_mem_gb = (free0 - torch.cuda.mem_get_info()[0]) / 1e9   # context, hierarchies, Krylov bases
     ms, units = aggregate_ranks(ms, s * n * args.steps, dist, device="cuda")
     value = units / (ms * 1e-3)
     its = st["iterations"] / max(st["steps"], 1)
@@ -339,6 +341,7 @@ def run_ours(args):
                    "krylov": "FGMRES(30) rtol 1e-10", "parallelism": f"replicas x{world}",
                    "l2": "working set > L2 (Krylov bases 1.3 GB); no flush"},
         "iterations_per_step": its, "resid": st["resid"], "setup_s": setup_s,
+        "device_mem_gb": round(device_mem_gb, 2),
         "clocks": clk.summary(), "gpu_launches": launches,
     }
     if args.launch_list:
