@@ -252,6 +252,35 @@ def test_table5_small_sizes_through_irk_solve():
                 ctx.close()
 
 
+def test_table8_small_sizes_left_through_irk_solve():
+    """The paper's left-preconditioned table (Table 8) at h_x^-1 = 8 and 16
+    through the library (left GMRES, FP64 AMG, which is a dense solve here):
+    J, GSL, DU and LD counts within max(2, 10%) of the printed ones."""
+    import json
+    import os
+    from paper_2010_11377_gb300 import problems
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_table8_radau_p2_left.json")) as f:
+        ref = json.load(f)
+    for N in (8, 16):
+        p = problems.heat_p2(N)
+        for s_ in range(2, 7):
+            A, b, c = B().irk_butcher_table("radau_iia", s_)
+            h = (1.0 / N) ** (3.0 / (2 * s_ - 1))
+            kstar = dev(synth.random_stage_block(p["n"], s_, 1000 + N).ravel())
+            for q, kind in enumerate(ref["columns"]):
+                if kind == "GSL_OPT":
+                    continue
+                o = B().irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64")
+                ctx = B().irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o)
+                rhs = torch.empty_like(kstar)
+                B().irk_apply_operator(ctx, kstar, rhs)
+                k = torch.empty_like(kstar)
+                st = B().irk_solve(ctx, rhs, k)
+                paper = ref["iterations"][str(N)][str(s_)][q]
+                assert abs(st["iterations"] - paper) <= max(2, int(np.ceil(0.1 * paper))), (N, s_, kind)
+                ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("kind", ["GSL", "LD"])
 def test_supg_nitsche_steps(prec, kind):
