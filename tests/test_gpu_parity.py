@@ -76,7 +76,7 @@ def oracle_amg_opts():
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("s", [1, 3, 7])
+@pytest.mark.parametrize("s", [1, 3, 7, 8])
 def test_operator_parity(s):
     mesh, prob = heat(41)
     A, _, _ = obt.radau_iia(s)
@@ -402,6 +402,24 @@ def test_lobatto_iiic_steps(kind, s):
         assert err < 1e-8, (t, err)
         assert _its_close(st["iterations"], amg_sol.step(refs[t]).iterations)
         u = out
+
+
+@pytest.mark.parametrize("s,restart", [(8, 30), (3, 1), (3, 64)])
+def test_limits_stage_count_and_restart(s, restart):
+    """The largest stage count (s = 8) and the restart limits (FGMRES(1) and
+    FGMRES(64)): a step within 1e-8 of the oracle's exact stage solve."""
+    mesh, prob = heat(26)
+    A, b, _ = obt.radau_iia(s)
+    h = 1 / 32
+    ctx, At = oracle_ctx(prob, A, "LD", h, amg_prec="f32", b=b, restart=restart, **AMG_OPTS)
+    u0 = synth.heat_u0(mesh)
+    ref = oirk.IRKSolver(prob, A, b, h, kind=None).step(u0, direct=True).u
+    out = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    st = B().irk_step(ctx, dev(u0), out)
+    assert np.linalg.norm(host(out) - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert st["resid"] <= 1e-10
+    if restart == 1:
+        assert st["restarts"] >= st["iterations"] - 1
 
 
 @pytest.mark.parametrize("reorth,eta", [(1, 0.1), (0, 0.7071067811865476), (0, 0.1), (0, 0.0)])
