@@ -402,6 +402,7 @@ def run_sweep(args):
           the true residual respectively)
       t5  P2 heat, N in {8..128}, Radau IIA s = 2..7, h_t = h_x^(3/(2s-1)), manufactured
           b = A k*, rtol 1e-8, J / GSL / DU / LD (the setting of the paper's Table 5)
+      t6  as t5 with Lobatto IIIC, s = 2..5, h_t = h_x^(3/(2s-2)) (the paper's Table 6)
       t8  as t5 with left-preconditioned GMRES (preconditioned residual), FP64 AMG, and the
           optimised GSL too (the setting of the paper's Table 8)
       t12 SUPG + Nitsche double glazing, h_x^-1 in {64, 128}, eps in {0.04, 0.005}, s = 2..7,
@@ -490,6 +491,29 @@ def run_sweep(args):
                                       "dof": s * p["n"], "h_t": h, "precond": kind, "its": st["iterations"],
                                       "ms": round(st["ms"], 3), "resid": st["resid"], "err_vs_kstar": err}),
                           flush=True)
+                    ctx.close()
+    elif args.sweep == "t6":
+        # the paper's Lobatto IIIC table: P2 heat, h_t = h_x^(3/(2s-2)), manufactured b,
+        # right-preconditioned GMRES to 1e-8
+        for s in (2, 3, 4, 5):
+            A, b, c = B.irk_butcher_table("lobatto_iiic", s)
+            for N in (8, 16, 32, 64, 128):
+                p = problems.heat_p2(N)
+                h = (1.0 / N) ** (3.0 / (2 * s - 2))
+                kstar = torch.tensor(synth.random_stage_block(p["n"], s, 1000 + N).ravel(), device="cuda")
+                for kind in ("J", "GSL", "DU", "LD"):
+                    o = B.irk_default_options(kind=kind, rtol=1e-8)
+                    ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o)
+                    rhs = torch.empty_like(kstar)
+                    B.irk_apply_operator(ctx, kstar, rhs)
+                    k = torch.empty_like(kstar)
+                    B.irk_solve(ctx, rhs, k)
+                    st = B.irk_solve(ctx, rhs, k)
+                    err = float((k - kstar).norm() / kstar.norm())
+                    print(json.dumps({"sweep": "t6", "problem": "heat_p2", "method": "lobatto_iiic", "N": N,
+                                      "n": p["n"], "s": s, "dof": s * p["n"], "h_t": h, "precond": kind,
+                                      "its": st["iterations"], "ms": round(st["ms"], 3), "resid": st["resid"],
+                                      "err_vs_kstar": err}), flush=True)
                     ctx.close()
     elif args.sweep == "t8":
         # the paper's left-preconditioned comparison (Table 8): P2 heat, manufactured b,
@@ -666,7 +690,7 @@ def main():
     ap.add_argument("--kernel-j", type=int, default=22, help="Gram-Schmidt basis index for --kernel")
     ap.add_argument("--kernel-warm", type=int, default=3)
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t8", "t12"],
+    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t12"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--launch-list", action="store_true",

@@ -252,6 +252,33 @@ def test_table5_small_sizes_through_irk_solve():
                 ctx.close()
 
 
+def test_table6_lobatto_small_sizes_through_irk_solve():
+    """The paper's Lobatto IIIC table (Table 6) at h_x^-1 = 8 and 16 through the
+    library (P2, FP32 AMG = a dense solve here, manufactured right-hand side,
+    rtol 1e-8): every count within max(3, 10%) of the printed one."""
+    import json
+    import os
+    from paper_2010_11377_gb300 import problems
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_table6_lobatto_p2.json")) as f:
+        ref = json.load(f)
+    for N in (8, 16):
+        p = problems.heat_p2(N)
+        for s_ in range(2, 6):
+            A, b, c = B().irk_butcher_table("lobatto_iiic", s_)
+            h = (1.0 / N) ** (3.0 / (2 * s_ - 2))
+            kstar = dev(synth.random_stage_block(p["n"], s_, 1000 + N).ravel())
+            for q, kind in enumerate(ref["columns"]):
+                o = B().irk_default_options(kind=kind, rtol=1e-8)
+                ctx = B().irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o)
+                rhs = torch.empty_like(kstar)
+                B().irk_apply_operator(ctx, kstar, rhs)
+                k = torch.empty_like(kstar)
+                st = B().irk_solve(ctx, rhs, k)
+                paper = ref["iterations"][str(N)][str(s_)][q]
+                assert abs(st["iterations"] - paper) <= max(3, int(np.ceil(0.1 * paper))), (N, s_, kind)
+                ctx.close()
+
+
 def test_table8_small_sizes_left_through_irk_solve():
     """The paper's left-preconditioned table (Table 8) at h_x^-1 = 8 and 16
     through the library (left GMRES, FP64 AMG, which is a dense solve here):
