@@ -479,7 +479,7 @@ def run_sweep(args):
                 h = (1.0 / N) ** (3.0 / (2 * s - 1))
                 kstar = torch.tensor(synth.random_stage_block(p["n"], s, 1000 + N).ravel(), device="cuda")
                 for kind in ("J", "GSL", "DU", "LD"):
-                    o = B.irk_default_options(kind=kind, rtol=1e-8)
+                    o = B.irk_default_options(kind=kind, rtol=1e-8, strength=args.strength)
                     ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o)
                     rhs = torch.empty_like(kstar)
                     B.irk_apply_operator(ctx, kstar, rhs)
@@ -488,7 +488,8 @@ def run_sweep(args):
                     st = B.irk_solve(ctx, rhs, k)
                     err = float((k - kstar).norm() / kstar.norm())
                     print(json.dumps({"sweep": "t5", "problem": "heat_p2", "N": N, "n": p["n"], "s": s,
-                                      "dof": s * p["n"], "h_t": h, "precond": kind, "its": st["iterations"],
+                                      "dof": s * p["n"], "h_t": h, "precond": kind, "strength": args.strength,
+                                      "its": st["iterations"],
                                       "ms": round(st["ms"], 3), "resid": st["resid"], "err_vs_kstar": err}),
                           flush=True)
                     ctx.close()
@@ -502,7 +503,7 @@ def run_sweep(args):
                 h = (1.0 / N) ** (3.0 / (2 * s - 2))
                 kstar = torch.tensor(synth.random_stage_block(p["n"], s, 1000 + N).ravel(), device="cuda")
                 for kind in ("J", "GSL", "DU", "LD"):
-                    o = B.irk_default_options(kind=kind, rtol=1e-8)
+                    o = B.irk_default_options(kind=kind, rtol=1e-8, strength=args.strength)
                     ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o)
                     rhs = torch.empty_like(kstar)
                     B.irk_apply_operator(ctx, kstar, rhs)
@@ -512,6 +513,7 @@ def run_sweep(args):
                     err = float((k - kstar).norm() / kstar.norm())
                     print(json.dumps({"sweep": "t6", "problem": "heat_p2", "method": "lobatto_iiic", "N": N,
                                       "n": p["n"], "s": s, "dof": s * p["n"], "h_t": h, "precond": kind,
+                                      "strength": args.strength,
                                       "its": st["iterations"], "ms": round(st["ms"], 3), "resid": st["resid"],
                                       "err_vs_kstar": err}), flush=True)
                     ctx.close()
@@ -525,7 +527,8 @@ def run_sweep(args):
                 h = (1.0 / N) ** (3.0 / (2 * s - 1))
                 kstar = torch.tensor(synth.random_stage_block(p["n"], s, 1000 + N).ravel(), device="cuda")
                 for kind in ("J", "GSL", "GSL_OPT", "DU", "LD"):
-                    o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64")
+                    o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64",
+                                              strength=args.strength)
                     ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o)
                     rhs = torch.empty_like(kstar)
                     B.irk_apply_operator(ctx, kstar, rhs)
@@ -534,7 +537,8 @@ def run_sweep(args):
                     st = B.irk_solve(ctx, rhs, k)
                     err = float((k - kstar).norm() / kstar.norm())
                     print(json.dumps({"sweep": "t8", "problem": "heat_p2", "N": N, "n": p["n"], "s": s,
-                                      "dof": s * p["n"], "h_t": h, "precond": kind, "its": st["iterations"],
+                                      "dof": s * p["n"], "h_t": h, "precond": kind, "strength": args.strength,
+                                      "its": st["iterations"],
                                       "ms": round(st["ms"], 3), "resid": st["resid"], "err_vs_kstar": err}),
                           flush=True)
                     ctx.close()
@@ -690,6 +694,8 @@ def main():
     ap.add_argument("--kernel-j", type=int, default=22, help="Gram-Schmidt basis index for --kernel")
     ap.add_argument("--kernel-warm", type=int, default=3)
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--strength", type=int, default=0, choices=[0, 1],
+                    help="AMG strength measure for the P2 sweeps (t5 t6 t8): 0 |a_ij|, 1 max(-a_ij, 0)")
     ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t12"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)

@@ -112,6 +112,11 @@ typedef struct {
   int32_t p_smooth;      /* damped-Jacobi steps smoothing the tentative prolongator,
                             P = (I - omega D^{-1} A)^p_smooth P_t, 1 or 2 (default 2); the
                             second step only on levels with at most 80 entries per row */
+  int32_t strength;      /* coupling measure of the strength test (c_ij + c_ji)/2 >= theta
+                            sqrt(|a_ii a_jj|): 0 = |a_ij| (default), 1 = max(-a_ij, 0);
+                            the negative-only measure helps P2 heat blocks but can leave a
+                            convection-dominated block without strong couplings (no
+                            coarsening) */
 } irk_options;
 
 typedef struct {
@@ -150,7 +155,7 @@ irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, 
 /* Fill *opt with the defaults: P_LD, FP32 AMG, Chebyshev degree 4 on [0.1, 1],
  * V(1,1), theta 0.08, coarse_max 2048, 12 levels, FGMRES(30), rtol 1e-10,
  * max_it 1000, selective reorthogonalisation (reorth_eta 0.1), right preconditioning,
- * two prolongator smoothing steps. */
+ * two prolongator smoothing steps, strength from |a_ij|. */
 void irk_default_options(irk_options* opt);
 
 /* ------------------------------------------------------------------------- *

@@ -5,9 +5,9 @@ by one AMG V-cycle (Section 4.2) using smoothed aggregation from IFISS
 (Section 5).  The paper gives no further parameters; this module follows the
 reading fixed in the design notes, step by step:
 
-  strength   i ~ j strong iff  (|a_ij| + |a_ji|)/2 >= theta_l sqrt(|a_ii a_jj|)
-             (symmetrised so that nonsymmetric blocks give an undirected
-             graph); theta_l starts at theta (0.08) on every level and is
+  strength   i ~ j strong iff  (c_ij + c_ji)/2 >= theta_l sqrt(|a_ii a_jj|) with
+             c_ij = |a_ij| (default; max(-a_ij, 0) as an option), symmetrised
+             so that nonsymmetric blocks give an undirected graph; theta_l starts at theta (0.08) on every level and is
              halved, at most 6 times, while more than a quarter of the level's
              nodes have no strong coupling (isotropic or mass-dominated blocks
              whose couplings all sit just below the threshold).
@@ -75,15 +75,17 @@ def priority_keys(n: int, level: int) -> np.ndarray:
     return (x << np.uint64(32)) | np.arange(n, dtype=np.uint64)
 
 
-def strength_graph(A: sp.csr_matrix, theta: float) -> sp.csr_matrix:
+def strength_graph(A: sp.csr_matrix, theta: float, negative: bool = False) -> sp.csr_matrix:
     """Boolean symmetric strength graph (no diagonal) as CSR with sorted
-    indices."""
+    indices.  negative: couplings measured by max(-a_ij, 0) (the off-diagonal
+    entries that carry the smooth error in an M-matrix-like block; quadratic
+    elements have positive ones), else by |a_ij|."""
     A = A.tocsr()
     A.sort_indices()
     n = A.shape[0]
     d = np.abs(A.diagonal())
-    absA = abs(A)
-    S = 0.5 * (absA + absA.T)          # (|a_ij| + |a_ji|) / 2
+    absA = (-A).maximum(0) if negative else abs(A)
+    S = 0.5 * (absA + absA.T)          # (c_ij + c_ji) / 2
     S = S.tocoo()
     keep = (S.row != S.col) & (S.data >= theta * np.sqrt(d[S.row] * d[S.col]))
     G = sp.csr_matrix((np.ones(int(keep.sum()), dtype=np.int8),
@@ -170,7 +172,7 @@ class Hierarchy:
 
     def __init__(self, A, theta=0.08, coarse_max=2048, max_levels=12,
                  nu_pre=1, nu_post=1, smoother="chebyshev", cheb_degree=4,
-                 cheb_lo=0.1, p_smooth=2):
+                 cheb_lo=0.1, p_smooth=2, strength_negative=False):
         self.theta = theta
         self.nu_pre = nu_pre
         self.nu_post = nu_post
@@ -186,12 +188,12 @@ class Hierarchy:
             if lev.n <= coarse_max or len(self.levels) >= max_levels:
                 break
             th = theta
-            G = strength_graph(lev.A, th)
+            G = strength_graph(lev.A, th, strength_negative)
             for _ in range(6):
                 if 4 * int(np.sum(np.diff(G.indptr) == 0)) <= lev.n:
                     break
                 th *= 0.5
-                G = strength_graph(lev.A, th)
+                G = strength_graph(lev.A, th, strength_negative)
             agg, _ = aggregate(G, lvl)
             nc = int(agg.max()) + 1
             if 10 * nc > 9 * lev.n:

@@ -3,7 +3,8 @@
 // IFISS smoothed aggregation and fixes no further parameter).
 //
 // Per level:
-//   strength   (|a_ij| + |a_ji|)/2 >= theta_l sqrt(|a_ii a_jj|)  (symmetric graph);
+//   strength   (c_ij + c_ji)/2 >= theta_l sqrt(|a_ii a_jj|), c_ij = |a_ij| (option: max(-a_ij, 0))
+//              (or |a_ij|), a symmetric graph;
 //              theta_l = theta, halved (at most 6 times) while more than a
 //              quarter of the level's nodes have no strong coupling
 //   roots      maximal distance-2 independent set chosen by fixed 64-bit
@@ -81,8 +82,8 @@ __global__ void k_diag(int n, const int* __restrict__ rp, const int* __restrict_
 // strength flags per entry and strong count per row
 __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ col,
                            const double* __restrict__ val, const double* __restrict__ diag,
-                           double theta, unsigned char* __restrict__ strong, int* __restrict__ cnt,
-                           int* __restrict__ niso) {
+                           double theta, int negative, unsigned char* __restrict__ strong,
+                           int* __restrict__ cnt, int* __restrict__ niso) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int c0 = 0;
@@ -92,7 +93,9 @@ __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restr
     unsigned char s = 0;
     if (c != r) {
       double aji = find_entry(rp, col, val, c, r);
-      double sij = (fabs(val[k]) + fabs(aji)) * 0.5;
+      double cij = negative ? fmax(-val[k], 0.0) : fabs(val[k]);
+      double cji = negative ? fmax(-aji, 0.0) : fabs(aji);
+      double sij = (cij + cji) * 0.5;
       double thr = theta * sqrt(dr * fabs(diag[c]));
       s = (sij >= thr) ? 1 : 0;
     }
@@ -420,7 +423,8 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
   double theta_l = p.theta;
   for (int halving = 0;; ++halving) {
     CK(cudaMemsetAsync(niso, 0, sizeof(int), st));
-    k_strength<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, theta_l, strong, scnt, niso);
+    k_strength<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, theta_l, p.strength_negative, strong, scnt,
+                                      niso);
     CK_LAUNCH();
     if (halving == 6 || 4 * int64_t(rd(niso, st)) <= int64_t(n)) break;
     theta_l *= 0.5;

@@ -409,6 +409,7 @@ void irk_default_options(irk_options* o) {
   o->reorth_eta = 0.1;
   o->side = 0;
   o->p_smooth = 2;
+  o->strength = 0;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -449,6 +450,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     return set_err(nullptr, IRK_ERR_INVALID, "reorth must be 0 or 1 and 0 <= reorth_eta < 1");
   if (o.side != 0 && o.side != 1) return set_err(nullptr, IRK_ERR_INVALID, "side must be 0 (right) or 1 (left)");
   if (o.p_smooth < 1 || o.p_smooth > 2) return set_err(nullptr, IRK_ERR_INVALID, "p_smooth must be 1 or 2");
+  if (o.strength != 0 && o.strength != 1) return set_err(nullptr, IRK_ERR_INVALID, "strength must be 0 or 1");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
     return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..2048");
   const irk_csr& M = prob->M;
@@ -491,6 +493,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     c.amg.cheb_degree = o.cheb_degree;
     c.amg.cheb_lo = o.cheb_lo;
     c.amg.p_smooth = o.p_smooth;
+    c.amg.strength_negative = o.strength;
     c.amg.nu_pre = o.nu_pre;
     c.amg.nu_post = o.nu_post;
     c.amg.amg_prec = o.amg_prec;

@@ -211,6 +211,7 @@ struct AmgParams {
   int nu_pre = 1, nu_post = 1;
   int amg_prec = 32;
   int p_smooth = 2;        // damped-Jacobi steps on the tentative prolongator
+  int strength_negative = 0;   // strength from max(-a_ij, 0) (else |a_ij|)
 };
 
 // Chebyshev step coefficients: step i updates d_i = alpha_i d_{i-1} + beta_i D^{-1}(b - A x_i)

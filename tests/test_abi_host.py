@@ -148,7 +148,7 @@ def test_fem_quad_rule_exact_degree4(L):
 
 
 @pytest.mark.parametrize("field,value", [("reorth_eta", 1.0), ("reorth_eta", -0.1), ("reorth", 2),
-                                         ("restart", 0), ("coarse_max", 4096), ("cheb_degree", 0), ("p_smooth", 0),
+                                         ("restart", 0), ("coarse_max", 4096), ("cheb_degree", 0), ("p_smooth", 0), ("strength", 2),
                                          ("side", 2)])
 def test_setup_rejects_bad_options_before_device_work(L, field, value):
     """Option validation happens on the host, before any CUDA call: a bad

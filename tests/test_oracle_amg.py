@@ -159,3 +159,24 @@ def test_prolongator_is_jacobi_power(steps):
     assert np.abs(P.toarray() - ref).max() <= 1e-14
     rho = np.max(np.abs(Ad).sum(axis=1) / np.abs(np.diag(Ad)))
     assert omega == 4.0 / (3.0 * rho)
+
+
+def test_strength_on_negative_couplings():
+    """The negative-coupling strength option counts only negative couplings: for a
+    block with nonpositive off-diagonals it equals the |a_ij| graph; positive
+    off-diagonal entries (as in quadratic elements) are never strong; a P2
+    stiffness-dominated block has positive entries, so the two graphs differ."""
+    A = _block(11)
+    Ap = (A - sp.diags(A.diagonal())).tocsr()
+    Ap.data = np.minimum(Ap.data, 0.0)            # an M-matrix with the same diagonal
+    M = (Ap + sp.diags(A.diagonal())).tocsr()
+    Gn = amg.strength_graph(M, 0.08, negative=True)
+    Ga = amg.strength_graph(M, 0.08, negative=False)
+    assert (Gn != Ga).nnz == 0
+    Pos = (abs(Ap) + sp.diags(A.diagonal())).tocsr()  # the same magnitudes, all positive
+    assert amg.strength_graph(Pos, 0.08, negative=True).nnz == 0
+    assert amg.strength_graph(Pos, 0.08, negative=False).nnz == Ga.nnz
+    mesh = synth.structured_mesh_p2(6)
+    K = fem.heat_problem_p2(mesh).F
+    assert (K > 0).sum() > K.shape[0]                # positive off-diagonals exist
+    assert (amg.strength_graph(K, 0.08, True) != amg.strength_graph(K, 0.08, False)).nnz > 0
