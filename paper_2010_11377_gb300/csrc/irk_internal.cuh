@@ -158,6 +158,7 @@ struct MatT {
   Sell sell;                 // lanes == 1
   int* rowptr = nullptr;     // lanes > 1
   int* col = nullptr;
+  short* dcol = nullptr;     // lanes > 1, square: 16-bit column offsets from the row, or null
   void* val = nullptr;       // CSR values (V-cycle precision, or BF16)
   int64_t stored() const { return lanes == 1 ? sell.nnz_pad : nnz; }
 };
@@ -169,13 +170,13 @@ struct LMat {
   const int* __restrict__ rowptr;
   const int* __restrict__ col;
   const V* __restrict__ val;
-  const short* __restrict__ dcol;   // SELL 16-bit column offsets, or null
+  const short* __restrict__ dcol;   // 16-bit column offsets from the row (SELL or CSR), or null
 };
 
 template <typename V>
 inline LMat<V> lmat(const MatT& m) {
   if (m.lanes == 1) return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell), m.sell.dcol};
-  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), nullptr};
+  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), m.dcol};
 }
 
 // ---------------------------------------------------------------------------

@@ -64,7 +64,8 @@ bool pdl_enabled() {
   return on == 1;
 }
 
-// 16-bit SELL column offsets (IRK_SELL16=0 keeps 32-bit columns everywhere)
+// 16-bit column offsets in the SELL and CSR layouts of square operators
+// (IRK_SELL16=0 keeps 32-bit columns everywhere)
 static bool sell_offsets_enabled() {
   static int on = -1;
   if (on < 0) {
@@ -304,6 +305,23 @@ __global__ void k_sell_offsets(int n, int nslices, const int* __restrict__ rowpt
   if (bad) atomicOr(overflow, 1);
 }
 
+// the same for CSR (one thread per row)
+__global__ void k_csr_offsets(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                              short* __restrict__ dcol, int* __restrict__ overflow) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  bool bad = false;
+  for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+    int d = col[k] - r;
+    if (d < -32767 || d > 32767) {
+      bad = true;
+      d = 0;
+    }
+    dcol[k] = static_cast<short>(d);
+  }
+  if (bad) atomicOr(overflow, 1);
+}
+
 void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, DevPool& pool,
                  cudaStream_t st) {
   S.n = A.n;
@@ -500,6 +518,16 @@ static void build_layout(const CsrD& A, MatT& m, int prec, int lanes, DevPool& p
   if (A.nnz) {
     k_convert_vals<<<nblk(A.nnz), 256, 0, st>>>(A.nnz, A.val, v64, v32, v16);
     CK_LAUNCH();
+  }
+  m.dcol = nullptr;
+  if (A.nnz > 0 && A.ncols == A.n && sell_offsets_enabled()) {
+    short* dc = pool.get<short>(A.nnz);
+    Tmp tmp;
+    int* ovf = tmp.get<int>(1);
+    CK(cudaMemsetAsync(ovf, 0, sizeof(int), st));
+    k_csr_offsets<<<nblk(A.n), 256, 0, st>>>(A.n, A.rowptr, A.col, dc, ovf);
+    CK_LAUNCH();
+    if (read_scalar(ovf, st) == 0) m.dcol = dc;
   }
 }
 

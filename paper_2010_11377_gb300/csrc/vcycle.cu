@@ -72,7 +72,12 @@ __device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
   } else {
     if (r >= 0) {
       int e = A.rowptr[r + 1];
-      for (int k = A.rowptr[r] + lane; k < e; k += L) acc = fma(widen(A.val[k]), xf(A.col[k]), acc);
+      if (A.dcol) {
+        for (int k = A.rowptr[r] + lane; k < e; k += L)
+          acc = fma(widen(A.val[k]), xf(r + static_cast<int>(A.dcol[k])), acc);
+      } else {
+        for (int k = A.rowptr[r] + lane; k < e; k += L) acc = fma(widen(A.val[k]), xf(A.col[k]), acc);
+      }
     }
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
@@ -234,7 +239,7 @@ struct VCycle {
 
   template <typename V>
   void count_matvec(const Level& L, int vec_reads, int vec_writes) {
-    const double idx_bytes = (L.Am.lanes == 1 && L.Am.sell.dcol) ? 2.0 : 4.0;   // 16-bit SELL offsets
+    const double idx_bytes = (L.Am.lanes == 1 ? L.Am.sell.dcol : L.Am.dcol) ? 2.0 : 4.0;   // 16-bit offsets
     cost.bytes += double(L.nnz) * (idx_bytes + sizeof(V)) + double(L.n) * sizeof(T) * (vec_reads + vec_writes);
     cost.flops += 2.0 * double(L.nnz) + 4.0 * L.n;
   }
