@@ -320,6 +320,16 @@ void irk_batch_destroy(irk_batch* b);
  * I (x) M^T + h_t A^T (x) F^T (symmetric M, F).  s*n each. */
 irk_status irk_apply_operator(irk_ctx* ctx, const double* d_z, double* d_w, int32_t transpose);
 
+/* The same operator on an FP32 d_z (s*n floats), as FGMRES applies it to the
+ * FP32/BF16 preconditioner outputs z_j = P^{-1} v_j (Section 4.2); d_w (s*n)
+ * is FP64.  Single-float pair arithmetic: each FP64 entry of M, F and h_t A is
+ * split into two floats, products are exact up to the split (2^-48 relative),
+ * sums carry their rounding errors, so |w - A z| is about 2^-47 times the sum
+ * of the absolute terms of each row (FP64: 2^-53).  When the environment sets
+ * IRK_KRON_FF=0, or an entry of M, F or h_t A lies outside [2^-64, 2^64], the
+ * product is taken in FP64 on the widened z instead. */
+irk_status irk_apply_operator_f32(irk_ctx* ctx, const float* d_z, double* d_w, int32_t transpose);
+
 /* d_z = P^{-1} d_v by the substitutions of Section 4.2, one V-cycle per
  * diagonal block (transpose != 0: P^T).  s*n each; the result is rounded to
  * the AMG precision before it is returned in FP64. */

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("irk_batch_adjoint", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(IrkStats), c_double_p]),
     ("irk_batch_destroy", None, [C.c_void_p]),
     ("irk_apply_operator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    ("irk_apply_operator_f32", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("irk_apply_precond", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("irk_vcycle", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("irk_residual_norm", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, c_double_p]),

@@ -330,6 +330,15 @@ def irk_apply_operator(ctx: Context, z, w, transpose=False):
     check(lib().irk_apply_operator(ctx.ptr, _dev(z), _dev(w), int(bool(transpose))), ctx.ptr)
 
 
+def irk_apply_operator_f32(ctx: Context, z, w, transpose=False):
+    """w (FP64) = the stage operator applied to an FP32 z, as FGMRES applies it
+    to FP32 preconditioner outputs."""
+    import torch
+    if not (z.is_cuda and z.dtype == torch.float32 and z.is_contiguous()):
+        raise ValueError("z must be a contiguous float32 CUDA tensor")
+    check(lib().irk_apply_operator_f32(ctx.ptr, C.c_void_p(z.data_ptr()), _dev(w), int(bool(transpose))), ctx.ptr)
+
+
 def irk_apply_precond(ctx: Context, v, z, transpose=False):
     check(lib().irk_apply_precond(ctx.ptr, _dev(v), _dev(z), int(bool(transpose))), ctx.ptr)
 

@@ -528,6 +528,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     c.Fc.col = c.Mc.col;
     irk::csr_to_sell(c.Mc, c.Ms, 1, 0, 0, c.pool, c.stream);
     irk::sell_share_pattern(c.Ms, c.Fc.val, c.Fc, c.Fs, 1, 1, c.pool, c.stream);
+    irk::kron_split_build(c);
     c.g = c.pool.get<double>(c.n);
     if (prob->g) CK(cudaMemcpy(c.g, prob->g, sizeof(double) * c.n, cudaMemcpyHostToDevice));
     else CK(cudaMemset(c.g, 0, sizeof(double) * c.n));
@@ -727,6 +728,7 @@ irk_status irk_set_kappa(irk_ctx* h, const double* d_kappa) {
     c.pool.release(c.Fs.v64);
     c.pool.release(c.Fs.v32);
     irk::sell_share_pattern(c.Ms, c.Fc.val, c.Fc, c.Fs, 1, 1, c.pool, c.stream);
+    irk::kron_split_build(c);
     irk::destroy_graphs(c);
     irk::build_hierarchies(c);
     irk::end_call(c);
@@ -739,6 +741,17 @@ irk_status irk_apply_operator(irk_ctx* h, const double* d_z, double* d_w, int32_
     Ctx& c = h->c;
     irk::begin_call(c);
     irk::kron_apply_plain(c, d_z, d_w, transpose != 0, c.stream);
+    c.launches += 1;
+    irk::end_call(c);
+  });
+}
+
+irk_status irk_apply_operator_f32(irk_ctx* h, const float* d_z, double* d_w, int32_t transpose) {
+  if (!h || !d_z || !d_w) return set_err(h, IRK_ERR_INVALID, "NULL argument");
+  return guarded(h, [&] {
+    Ctx& c = h->c;
+    irk::begin_call(c);
+    irk::kron_apply_f32(c, d_z, d_w, transpose != 0, c.stream);
     c.launches += 1;
     irk::end_call(c);
   });
@@ -858,7 +871,9 @@ irk_status irk_profile(irk_ctx* h, int32_t which, int32_t j, int32_t warm, int32
       case IRK_PROF_KRON: {
         launch = [&] { irk::profile_kron_launch(c, c.stream); };
         double zs = c.amg.amg_prec == 64 ? 8.0 : 4.0;
-        B = double(c.Mc.nnz) * 20.0 + double(c.N) * (zs + 8.0);
+        const double idx = c.Ms.dcol ? 2.0 : 4.0;
+        // per nonzero: M and F (two FP64, or one float4 of single-float pairs) and its column
+        B = double(c.Mc.nnz) * (16.0 + idx) + double(c.N) * (zs + 8.0);
         Fl = 2.0 * (2.0 * c.s * double(c.Mc.nnz) + double(c.s) * c.s * c.n);
         break;
       }

@@ -259,6 +259,11 @@ struct KronCoef {          // h A (or h A^T), row-major MAX_S x MAX_S
   double a[MAX_S * MAX_S];
 };
 
+struct KronCoefF {         // the same as single-float pairs: a = hi + lo (to 2^-48 |a|)
+  float hi[MAX_S * MAX_S];
+  float lo[MAX_S * MAX_S];
+};
+
 struct SweepPlan {         // substitution order and couplings of P^{-1}
   int s;
   int order[MAX_S];                // stage processed at position p
@@ -308,6 +313,7 @@ struct Ctx {
   // problem
   CsrD Mc, Fc;              // FP64 CSR, one pattern
   Sell Ms, Fs;              // SELL-32: Ms.v64 = M, Fs.v64 = F (FP64), Fs.v32 = F (FP32)
+  float4* MFs = nullptr;    // SELL-32 {M hi, M lo, F hi, F lo} single-float pairs, or null
   double* g = nullptr;      // lift (n)
   bool symmetric = false;
 
@@ -324,6 +330,7 @@ struct Ctx {
   double A[MAX_S * MAX_S], b[MAX_S], c[MAX_S], At[MAX_S * MAX_S];
   int kind = IRK_PC_LD;
   KronCoef K, KT;
+  KronCoefF Kf, KTf;
   SweepPlan plan, planT;
   AmgParams amg;
   SmoothCoef sc;
@@ -378,6 +385,10 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
                  cudaStream_t st);
 void sell_share_pattern(const Sell& pat, const double* csr_vals, const CsrD& A, Sell& S, int want64,
                         int want32, DevPool& pool, cudaStream_t st);
+// single-float pair copies of M, F and h A for the operator on FP32 vectors
+// (MFs stays null when disabled or when an entry is outside [2^-64, 2^64])
+void kron_split_build(Ctx& c);
+void kron_apply_f32(Ctx& c, const float* z, double* w, bool transpose, cudaStream_t st);
 void csr_transpose(const CsrD& A, CsrD& T, DevPool& pool, cudaStream_t st);
 int choose_lanes(int64_t nnz, int n);
 int autotune_lanes(const CsrD& A, int prec, cudaStream_t st);

@@ -13,6 +13,7 @@
 #include "irk_internal.cuh"
 
 #include <cmath>
+#include <cstdlib>
 
 namespace irk {
 
@@ -259,6 +260,100 @@ k_kron(int n, SellView<double> Mv, const double* __restrict__ Fval, JPtr<const T
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// The operator on FP32 vectors (the FGMRES product on FP32 preconditioner
+// outputs) in single-float pair arithmetic, off the narrow FP64 pipe.  An FP64
+// entry m is held as hi + lo with hi = rn(m), lo = rn(m - hi), so that
+// |m - hi - lo| <= 2^-48 |m|.  A product of hi with an FP32 z is exact as p + e
+// (e the FMA residual, the error-free product of Ogita, Rump and Oishi 2005);
+// a sum h + p is exact as s + t (Knuth's TwoSum).  The accumulator (h, l) keeps
+// the rounded head in h and a float tail of the small terms in l, so a row sum
+// is off by about 2^-47 of the sum of its absolute terms (FP64 2^-53), and the
+// result h + l is formed in FP64 at the end.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ff_add(float& h, float& l, float p, float tail) {
+  const float s = __fadd_rn(h, p);
+  const float b = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, b)), __fsub_rn(p, b));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(err, tail));
+}
+
+// (h, l) += (ah + al) z
+__device__ __forceinline__ void ff_fma1(float& h, float& l, float ah, float al, float z) {
+  const float p = __fmul_rn(ah, z);
+  const float e = __fmaf_rn(ah, z, -p);
+  ff_add(h, l, p, __fmaf_rn(al, z, e));
+}
+
+// (h, l) += (ah + al)(bh + bl), the al bl term dropped (2^-48 relative)
+__device__ __forceinline__ void ff_fma2(float& h, float& l, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  ff_add(h, l, p, e);
+}
+
+// w = A z for FP32 z: one thread per row (grid-stride), {M hi, M lo, F hi,
+// F lo} of each nonzero in one 16-byte load, all s stages per nonzero.
+template <int S>
+__global__ void __launch_bounds__(BS)
+k_kron_ff(int n, SellView<double> Mv, const float4* __restrict__ mf, JPtr<const float> zp, JPtr<double> wp,
+          KronCoefF K, GmresState* st) {
+  pdl_trigger();
+  pdl_wait();
+  if (st && st->done) return;
+  const float* __restrict__ z = zp.get();
+  double* __restrict__ w = wp.get();
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    float mh[S], ml[S], fh[S], fl[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      mh[i] = 0.f;
+      ml[i] = 0.f;
+      fh[i] = 0.f;
+      fl[i] = 0.f;
+    }
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = Mv.sptr[sl];
+    int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
+    for (int k = 0; k < wdt; ++k) {
+      int64_t idx = base + (int64_t(k) << 5) + lane;
+      int c = sell_col(Mv.col, Mv.dcol, idx, r);
+      const float4 q = mf[idx];
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const float zz = z[int64_t(i) * n + c];
+        ff_fma1(mh[i], ml[i], q.x, q.y, zz);
+        ff_fma1(fh[i], fl[i], q.z, q.w, zz);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      float h = mh[i], l = ml[i];
+#pragma unroll
+      for (int j = 0; j < S; ++j) ff_fma2(h, l, K.hi[i * MAX_S + j], K.lo[i * MAX_S + j], fh[j], fl[j]);
+      w[int64_t(i) * n + r] = to_f64(h) + to_f64(l);
+    }
+  }
+}
+
+// {M hi, M lo, F hi, F lo}; flag entries outside [2^-64, 2^64] (other than 0)
+__global__ void k_split_ff(int64_t nnz, const double* __restrict__ m, const double* __restrict__ f,
+                           float4* __restrict__ out, int* __restrict__ bad) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= nnz) return;
+  const double a = m[i], b = f[i];
+  const double big = 18446744073709551616.0, small = 1.0 / 18446744073709551616.0;   // 2^64, 2^-64
+  const bool ok_a = a == 0.0 || (fabs(a) <= big && fabs(a) >= small);
+  const bool ok_b = b == 0.0 || (fabs(b) <= big && fabs(b) >= small);
+  if (!(ok_a && ok_b)) atomicOr(bad, 1);
+  const float ah = __double2float_rn(a), bh = __double2float_rn(b);
+  out[i] = make_float4(ah, __double2float_rn(a - static_cast<double>(ah)), bh,
+                       __double2float_rn(b - static_cast<double>(bh)));
 }
 
 // ---------------------------------------------------------------------------
@@ -676,7 +771,11 @@ int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
   const int* jp = &c.st->j;
   bool z32 = c.amg.amg_prec != 64;
   IRK_DISPATCH_S(c.s, {
-    if (z32)
+    if (z32 && c.MFs)
+      launch_k(k_kron_ff<S>, G, BS, 0, st, n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
+                                      JPtr<const float>{static_cast<const float*>(c.Z), jp, N, 0, 0},
+                                      JPtr<double>{c.V, jp, N, 1, 0}, transpose ? c.KTf : c.Kf, c.st);
+    else if (z32)
       launch_k(k_kron<S, float, 0>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64,
                                             JPtr<const float>{static_cast<const float*>(c.Z), jp, N, 0, 0},
                                             JPtr<double>{c.V, jp, N, 1, 0}, K, nullptr, c.st, c.partials);
@@ -938,7 +1037,11 @@ void profile_kron_launch(Ctx& c, cudaStream_t st) {
   unsigned G = row_grid(c);
   bool z32 = c.amg.amg_prec != 64;
   IRK_DISPATCH_S(c.s, {
-    if (z32)
+    if (z32 && c.MFs)
+      launch_k(k_kron_ff<S>, G, BS, 0, st, n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
+                                      JPtr<const float>{static_cast<const float*>(c.Z), nullptr, N, 0, 0},
+                                      JPtr<double>{c.V, nullptr, N, 1, 0}, c.Kf, nullptr);
+    else if (z32)
       launch_k(k_kron<S, float, 0>, G, BS, 0, st, n, view<double>(c.Ms), c.Fs.v64,
                                             JPtr<const float>{static_cast<const float*>(c.Z), nullptr, N, 0, 0},
                                             JPtr<double>{c.V, nullptr, N, 1, 0}, c.K, nullptr, nullptr, nullptr);
@@ -1004,6 +1107,63 @@ void kron_apply_plain(Ctx& c, const double* z, double* w, bool transpose, cudaSt
     launch_k(k_kron<S, double, 0>, row_grid(c), BS, 0, st, c.n, view<double>(c.Ms), c.Fs.v64,
                                                      JPtr<const double>{z, nullptr, 0, 0, 0},
                                                      JPtr<double>{w, nullptr, 0, 0, 0}, K, nullptr, nullptr, nullptr);
+  });
+  CK_LAUNCH();
+}
+
+// single-float pair operator on (IRK_KRON_FF=0: FP64 products on widened z)
+static bool kron_ff_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("IRK_KRON_FF");
+    on = (e && std::atoi(e) == 0) ? 0 : 1;
+  }
+  return on == 1;
+}
+
+static bool split_coef(const KronCoef& K, KronCoefF& F) {
+  bool ok = true;
+  for (int i = 0; i < MAX_S * MAX_S; ++i) {
+    const double a = K.a[i];
+    F.hi[i] = static_cast<float>(a);
+    F.lo[i] = static_cast<float>(a - static_cast<double>(F.hi[i]));
+    if (a != 0.0 && !(std::fabs(a) <= 0x1p64 && std::fabs(a) >= 0x1p-64)) ok = false;
+  }
+  return ok;
+}
+
+void kron_split_build(Ctx& c) {
+  if (c.MFs) {
+    c.pool.release(c.MFs);
+    c.MFs = nullptr;
+  }
+  bool ok = split_coef(c.K, c.Kf);
+  ok = split_coef(c.KT, c.KTf) && ok;
+  const int64_t np = c.Ms.nnz_pad;
+  if (!ok || !kron_ff_enabled() || c.amg.amg_prec == 64 || np <= 0 || !c.Ms.v64 || !c.Fs.v64) return;
+  float4* mf = c.pool.get<float4>(np);
+  Tmp tmp;
+  int* bad = tmp.get<int>(1);
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), c.stream));
+  k_split_ff<<<static_cast<unsigned>((np + 255) / 256), 256, 0, c.stream>>>(np, c.Ms.v64, c.Fs.v64, mf, bad);
+  CK_LAUNCH();
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  if (flag) c.pool.release(mf);
+  else c.MFs = mf;
+}
+
+void kron_apply_f32(Ctx& c, const float* z, double* w, bool transpose, cudaStream_t st) {
+  IRK_DISPATCH_S(c.s, {
+    if (c.MFs)
+      launch_k(k_kron_ff<S>, row_grid(c), BS, 0, st, c.n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
+                                        JPtr<const float>{z, nullptr, 0, 0, 0}, JPtr<double>{w, nullptr, 0, 0, 0},
+                                        transpose ? c.KTf : c.Kf, nullptr);
+    else
+      launch_k(k_kron<S, float, 0>, row_grid(c), BS, 0, st, c.n, view<double>(c.Ms), c.Fs.v64,
+                                              JPtr<const float>{z, nullptr, 0, 0, 0}, JPtr<double>{w, nullptr, 0, 0, 0},
+                                              transpose ? c.KT : c.K, nullptr, nullptr, nullptr);
   });
   CK_LAUNCH();
 }

@@ -96,6 +96,36 @@ def test_operator_parity(s):
     assert np.max(np.abs(host(y) - prob.M @ x)) < 1e-15 * np.max(np.abs(x))
 
 
+@pytest.mark.parametrize("s", [1, 3, 5, 8])
+def test_operator_f32_parity(s):
+    """The operator on FP32 vectors (the FGMRES product on FP32 preconditioner
+    outputs), computed in single-float pairs: against the oracle in FP64 on the
+    same (exactly widened) input.  Each term of a row carries at most 2^-47 of
+    its size (split of the FP64 entry plus the rounded low product), and the
+    float tail of the accumulator adds at most one 2^-24 rounding of itself per
+    term; with at most 16 terms per row (nonzeros plus stages) the bound is
+    16^2 2^-48 = 2^-40 of the row's sum of absolute terms."""
+    mesh, prob = heat(41)
+    A, _, _ = obt.radau_iia(s)
+    h = 1 / 64
+    ctx, _ = oracle_ctx(prob, A, "LD" if s > 1 else "J", h, amg_prec="f32")
+    z32 = synth.random_stage_block(prob.n, s, 12).astype(np.float32)
+    z = z32.astype(np.float64)
+    zd = torch.tensor(z32.ravel(), device="cuda")
+    for tr in (False, True):
+        w = torch.empty(s * prob.n, dtype=torch.float64, device="cuda")
+        B().irk_apply_operator_f32(ctx, zd, w, transpose=tr)
+        Am = A.T if tr else A
+        ref = oirk.apply_operator(prob.M, prob.F, Am, h, z)
+        absref = oirk.apply_operator(abs(prob.M), abs(prob.F), np.abs(Am), h, np.abs(z))
+        err = np.abs(host(w).reshape(s, -1) - ref)
+        assert np.all(err <= 2.0 ** -40 * absref), (err / absref).max()
+        w64 = torch.empty_like(w)
+        B().irk_apply_operator(ctx, dev(z.ravel()), w64, transpose=tr)
+        # the FP64 product on the same input, to the same bound
+        assert np.all(np.abs(host(w) - host(w64)).reshape(s, -1) <= 2.0 ** -40 * absref)
+
+
 @pytest.mark.parametrize("which", ["heat", "dg"])
 @pytest.mark.parametrize("p_smooth,strength", [(1, 0), (2, 1), (2, 0)])
 def test_aggregates_and_galerkin_parity(which, p_smooth, strength):
