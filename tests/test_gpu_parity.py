@@ -284,6 +284,35 @@ def test_table5_small_sizes_through_irk_solve():
                 ctx.close()
 
 
+def test_solve_scale_invariance():
+    """Right-hand sides scaled by 2^-100, 1e-30, 1 and 1e30: the solution
+    scales with them and the FGMRES iteration count stays the same (the
+    preconditioner and the single-float pair operator only see the unit
+    vectors sigma_j V_j), with exact zeros in the manufactured solution."""
+    mesh, prob = heat(60)
+    A, b, c = obt.radau_iia(3)
+    h = 1 / 64
+    ctx, _ = oracle_ctx(prob, A, "LD", h, amg_prec="f32", b=b, **AMG_OPTS)
+    kstar = synth.random_stage_block(prob.n, 3, 21).ravel()
+    kstar[::7] = 0.0
+    rhs = torch.empty(kstar.size, dtype=torch.float64, device="cuda")
+    B().irk_apply_operator(ctx, dev(kstar), rhs)
+    k1 = torch.empty_like(rhs)
+    st1 = B().irk_solve(ctx, rhs, k1)
+    assert float((k1 - dev(kstar)).norm() / np.linalg.norm(kstar)) < 1e-6
+    # a power of two scales every step exactly: the same iterates, scaled
+    k = torch.empty_like(rhs)
+    st = B().irk_solve(ctx, rhs * 2.0 ** -100, k)
+    assert st["iterations"] == st1["iterations"]
+    assert torch.equal(k * 2.0 ** 100, k1)
+    for scale in (1e-30, 1e30):
+        k = torch.empty_like(rhs)
+        st = B().irk_solve(ctx, rhs * scale, k)
+        assert abs(st["iterations"] - st1["iterations"]) <= 1, (scale, st["iterations"], st1["iterations"])
+        assert st["resid"] <= 1e-10
+        assert float((k / scale - k1).norm() / k1.norm()) < 1e-6, scale
+
+
 def test_table6_lobatto_small_sizes_through_irk_solve():
     """The paper's Lobatto IIIC table (Table 6) at h_x^-1 = 8 and 16 through the
     library (P2, FP32 AMG = a dense solve here, manufactured right-hand side,
