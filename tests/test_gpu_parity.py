@@ -126,6 +126,28 @@ def test_operator_f32_parity(s):
         assert np.all(np.abs(host(w) - host(w64)).reshape(s, -1) <= 2.0 ** -40 * absref)
 
 
+def test_operator_f32_range_fallback():
+    """Matrix entries below 2^-64 (here M and F scaled by 2^-80) keep the FP32
+    input product in FP64: bit-identical to the FP64 operator on the widened
+    input.  At unit scale the single-float pair product is the one that runs
+    (it rounds differently somewhere, within the same bound)."""
+    mesh, prob = heat(33)
+    A, _, _ = obt.radau_iia(3)
+    h = 1 / 64
+    z32 = synth.random_stage_block(prob.n, 3, 13).astype(np.float32)
+    zd = torch.tensor(z32.ravel(), device="cuda")
+    z64 = dev(z32.astype(np.float64).ravel())
+    for scale, same in ((2.0 ** -80, True), (1.0, False)):
+        scaled = ofem.Problem((prob.M * scale).tocsr(), (prob.F * scale).tocsr(), prob.g, mesh)
+        ctx, _ = oracle_ctx(scaled, A, "LD", h, amg_prec="f32")
+        w32 = torch.empty(3 * prob.n, dtype=torch.float64, device="cuda")
+        w64 = torch.empty_like(w32)
+        B().irk_apply_operator_f32(ctx, zd, w32)
+        B().irk_apply_operator(ctx, z64, w64)
+        assert torch.equal(w32, w64) == same, scale
+        ctx.close()
+
+
 @pytest.mark.parametrize("which", ["heat", "dg"])
 @pytest.mark.parametrize("p_smooth,strength", [(1, 0), (2, 1), (2, 0)])
 def test_aggregates_and_galerkin_parity(which, p_smooth, strength):
