@@ -760,6 +760,10 @@ __global__ void k_convert(const void* in, int ip, void* out, int op, int64_t n) 
 
 static unsigned row_grid(const Ctx& c) { return static_cast<unsigned>(c.gs_grid); }
 
+// the pair operator is latency-bound (gathers of z, no FP64 pipe limit): one
+// row per thread, so the block scheduler keeps every SM at its register limit
+static unsigned ff_grid(const Ctx& c) { return static_cast<unsigned>(c.n > 0 ? (c.n + BS - 1) / BS : 1); }
+
 // One FGMRES iteration after the preconditioner: w = A z_j into V_{j+1},
 // Gram-Schmidt, Givens, and at a cycle end x += Z y and the true residual.
 int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
@@ -772,7 +776,7 @@ int fgmres_body_launch(Ctx& c, bool transpose, cudaStream_t st) {
   bool z32 = c.amg.amg_prec != 64;
   IRK_DISPATCH_S(c.s, {
     if (z32 && c.MFs)
-      launch_k(k_kron_ff<S>, G, BS, 0, st, n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
+      launch_k(k_kron_ff<S>, ff_grid(c), BS, 0, st, n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
                                       JPtr<const float>{static_cast<const float*>(c.Z), jp, N, 0, 0},
                                       JPtr<double>{c.V, jp, N, 1, 0}, transpose ? c.KTf : c.Kf, c.st);
     else if (z32)
@@ -1038,7 +1042,7 @@ void profile_kron_launch(Ctx& c, cudaStream_t st) {
   bool z32 = c.amg.amg_prec != 64;
   IRK_DISPATCH_S(c.s, {
     if (z32 && c.MFs)
-      launch_k(k_kron_ff<S>, G, BS, 0, st, n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
+      launch_k(k_kron_ff<S>, ff_grid(c), BS, 0, st, n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
                                       JPtr<const float>{static_cast<const float*>(c.Z), nullptr, N, 0, 0},
                                       JPtr<double>{c.V, nullptr, N, 1, 0}, c.Kf, nullptr);
     else if (z32)
@@ -1157,7 +1161,7 @@ void kron_split_build(Ctx& c) {
 void kron_apply_f32(Ctx& c, const float* z, double* w, bool transpose, cudaStream_t st) {
   IRK_DISPATCH_S(c.s, {
     if (c.MFs)
-      launch_k(k_kron_ff<S>, row_grid(c), BS, 0, st, c.n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
+      launch_k(k_kron_ff<S>, ff_grid(c), BS, 0, st, c.n, view<double>(c.Ms), static_cast<const float4*>(c.MFs),
                                         JPtr<const float>{z, nullptr, 0, 0, 0}, JPtr<double>{w, nullptr, 0, 0, 0},
                                         transpose ? c.KTf : c.Kf, nullptr);
     else
