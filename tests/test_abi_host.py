@@ -206,3 +206,81 @@ def test_fem_supg_nitsche_matches_oracle(L, eps):
     assert abs(M - o.M).max() <= 1e-15
     assert abs(F - o.F).max() <= 1e-14
     assert np.abs(p["g"] - o.g).max() <= 1e-14
+
+
+def _header_structs():
+    """Field names, in order, of every anonymous `typedef struct { ... } name;`
+    in include/irk.h."""
+    src = open(os.path.join(ROOT, "include", "irk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if decl:   # "type a" or "type a, b"
+                fields += [re.findall(r"(\w+)\s*$", part)[0] for part in decl.split(",")]
+        out[name] = fields
+    return out
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """The ctypes mirrors of the header's structs have the same fields in the
+    same order, and the same offsets and sizes as the C compiler gives them."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2010_11377_gb300 import _abi
+    mirrors = {"irk_csr": _abi.IrkCsr, "irk_butcher": _abi.IrkButcher, "irk_options": _abi.IrkOptions,
+               "irk_stats": _abi.IrkStats, "irk_problem": _abi.IrkProblem}
+    structs = _header_structs()
+    assert set(mirrors) <= set(structs), sorted(structs)
+    for name, cls in mirrors.items():
+        assert [f for f, _ in cls._fields_] == structs[name], name
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "irk.h"', "int main(void) {"]
+    for name, fields in structs.items():
+        if name not in mirrors:
+            continue
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    csrc = tmp_path / "layout.c"
+    csrc.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(csrc), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    checked = 0
+    for ln in got:
+        if not ln:
+            continue
+        name, field, value = ln.split()
+        cls = mirrors[name]
+        if field == "sizeof":
+            assert ctypes.sizeof(cls) == int(value), name
+        else:
+            assert getattr(cls, field).offset == int(value), (name, field)
+        checked += 1
+    assert checked > 30
+
+
+def test_default_options_as_documented(L):
+    """irk_default_options fills the values its declaration documents: P_LD, FP32
+    AMG, Chebyshev degree 4 on [0.1, 1], V(1,1), theta 0.08, coarse_max 2048,
+    12 levels, FGMRES(30), rtol 1e-10, max_it 1000, reorth_eta 0.1, right
+    preconditioning, two prolongator smoothing steps, strength from |a_ij|."""
+    import ctypes
+    from paper_2010_11377_gb300 import _abi
+    o = _abi.IrkOptions()
+    L.irk_default_options(ctypes.byref(o))
+    src = open(os.path.join(ROOT, "include", "irk.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"\b(IRK_[A-Z0-9_]+)\s*=\s*(-?\d+)", src))
+    assert o.kind == enum["IRK_PC_LD"]
+    assert o.amg_prec == enum["IRK_AMG_F32"]
+    assert (o.cheb_degree, o.cheb_lo, o.nu_pre, o.nu_post) == (4, 0.1, 1, 1)
+    assert (o.theta, o.coarse_max, o.max_levels) == (0.08, 2048, 12)
+    assert (o.restart, o.rtol, o.max_it) == (30, 1e-10, 1000)
+    assert (o.reorth, o.reorth_eta, o.side, o.p_smooth, o.strength) == (0, 0.1, 0, 2, 0)
