@@ -60,8 +60,9 @@ enum {
   IRK_PC_CUSTOM = 5   /* caller-given A~: diagonal, lower or upper triangular   */
 };
 
-/* Arithmetic of the AMG hierarchies and V-cycles (the outer FGMRES, the
- * operator apply, the true residual and the solution update are always FP64). */
+/* Arithmetic of the AMG hierarchies and V-cycles.  The FGMRES basis, the true
+ * residual and the solution update are always FP64; the operator on FP32
+ * preconditioner outputs runs in single-float pairs (irk_apply_operator_f32). */
 enum { IRK_AMG_F64 = 64, IRK_AMG_F32 = 32, IRK_AMG_BF16 = 16 /* BF16 finest matrix, FP32 elsewhere */ };
 
 enum { IRK_SMOOTH_L1JACOBI = 0, IRK_SMOOTH_CHEBYSHEV = 1 };
@@ -88,12 +89,12 @@ typedef struct {
   const double* Atilde;  /* s*s row-major, required for IRK_PC_CUSTOM, else ignored */
   int32_t amg_prec;      /* IRK_AMG_F64 / _F32 / _BF16 */
   int32_t smoother;      /* IRK_SMOOTH_* */
-  int32_t cheb_degree;   /* Chebyshev polynomial degree per sweep (1..8) */
-  double cheb_lo;        /* lower end of the Chebyshev interval [lo, 1] of D_l1^{-1} A */
+  int32_t cheb_degree;   /* Chebyshev polynomial degree per sweep (1..16) */
+  double cheb_lo;        /* lower end of the Chebyshev interval [lo, 1] of D_l1^{-1} A, 0 < lo < 1 */
   int32_t nu_pre, nu_post; /* V(nu_pre, nu_post) sweeps */
-  double theta;          /* strength threshold */
+  double theta;          /* strength threshold, 0 <= theta <= 1 */
   int32_t coarse_max;    /* coarsest level has at most this many rows (<= 2048) */
-  int32_t max_levels;    /* <= 16 */
+  int32_t max_levels;    /* 1..16 */
   int32_t restart;       /* FGMRES restart length m (1..64) */
   double rtol;           /* stop when ||b - A k||_2 <= rtol ||b||_2 */
   int32_t max_it;        /* total inner iterations per solve */

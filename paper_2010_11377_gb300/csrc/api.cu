@@ -439,6 +439,14 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   irk_options o;
   if (opt) o = *opt;
   else irk_default_options(&o);
+  if (o.kind < IRK_PC_J || o.kind > IRK_PC_CUSTOM) return set_err(nullptr, IRK_ERR_INVALID, "unknown preconditioner kind");
+  if (o.kind == IRK_PC_CUSTOM && !o.Atilde) return set_err(nullptr, IRK_ERR_INVALID, "IRK_PC_CUSTOM needs Atilde");
+  if (o.smoother != IRK_SMOOTH_L1JACOBI && o.smoother != IRK_SMOOTH_CHEBYSHEV)
+    return set_err(nullptr, IRK_ERR_INVALID, "unknown smoother");
+  if (!(o.cheb_lo > 0.0 && o.cheb_lo < 1.0)) return set_err(nullptr, IRK_ERR_INVALID, "cheb_lo must lie in (0, 1)");
+  if (!(o.theta >= 0.0 && o.theta <= 1.0)) return set_err(nullptr, IRK_ERR_INVALID, "theta must lie in [0, 1]");
+  if (o.max_levels < 1 || o.max_levels > irk::MAX_LEVELS)
+    return set_err(nullptr, IRK_ERR_INVALID, "max_levels must be 1..16");
   if (o.restart < 1 || o.restart > irk::MAX_M) return set_err(nullptr, IRK_ERR_INVALID, "restart must be 1..64");
   if (o.amg_prec != 64 && o.amg_prec != 32 && o.amg_prec != 16)
     return set_err(nullptr, IRK_ERR_INVALID, "amg_prec must be 64, 32 or 16");
@@ -456,6 +464,8 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   const irk_csr& M = prob->M;
   const irk_csr& F = prob->F;
   if (M.n != F.n || M.nnz != F.nnz || M.n < 1) return set_err(nullptr, IRK_ERR_INVALID, "M and F differ in size");
+  if (!M.rowptr || !F.rowptr || M.nnz < 0 || (M.nnz > 0 && (!M.col || !F.col || !M.val || !F.val)))
+    return set_err(nullptr, IRK_ERR_INVALID, "bad CSR matrix");
   for (int i = 0; i <= M.n; ++i)
     if (M.rowptr[i] != F.rowptr[i]) return set_err(nullptr, IRK_ERR_INVALID, "M and F must share one pattern");
   for (int64_t k = 0; k < M.nnz; ++k)

@@ -147,15 +147,10 @@ def test_fem_quad_rule_exact_degree4(L):
             assert abs(C[:, 1].sum() - exact) < 1e-14, (a, bexp)
 
 
-@pytest.mark.parametrize("field,value", [("reorth_eta", 1.0), ("reorth_eta", -0.1), ("reorth", 2),
-                                         ("restart", 0), ("coarse_max", 4096), ("cheb_degree", 0), ("p_smooth", 0), ("strength", 2),
-                                         ("side", 2)])
-def test_setup_rejects_bad_options_before_device_work(L, field, value):
-    """Option validation happens on the host, before any CUDA call: a bad
-    option returns IRK_ERR_INVALID with a message and no context."""
+def _setup_one_unknown(L, o, null_rowptr=False):
+    """irk_setup on a one-unknown problem; returns (status, context pointer)."""
     import ctypes as C
     from paper_2010_11377_gb300 import _abi as A
-    from paper_2010_11377_gb300.binding import irk_default_options
     rowptr = np.array([0, 1], dtype=np.int64)
     col = np.array([0], dtype=np.int32)
     val = np.array([1.0])
@@ -163,16 +158,45 @@ def test_setup_rejects_bad_options_before_device_work(L, field, value):
     Am, b, c = (np.ascontiguousarray(x, dtype=np.float64) for x in (Am, b, c))
     dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
     prob = A.IrkProblem()
-    prob.M = A.IrkCsr(1, 1, rowptr.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
-                      dp(val))
+    rp = None if null_rowptr else rowptr.ctypes.data_as(C.POINTER(C.c_int64))
+    prob.M = A.IrkCsr(1, 1, rp, col.ctypes.data_as(C.POINTER(C.c_int32)), dp(val))
     prob.F = prob.M
     bt = A.IrkButcher(2, dp(Am), dp(b), dp(c))
-    o = irk_default_options()
-    setattr(o, field, value)
     out = C.c_void_p()
     st = L.irk_setup(C.byref(prob), C.byref(bt), 0.1, C.byref(o), None, C.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("field,value", [("reorth_eta", 1.0), ("reorth_eta", -0.1), ("reorth", 2),
+                                         ("restart", 0), ("coarse_max", 4096), ("cheb_degree", 0), ("p_smooth", 0), ("strength", 2),
+                                         ("side", 2), ("kind", 6), ("kind", -1), ("smoother", 2),
+                                         ("cheb_lo", 0.0), ("cheb_lo", 1.0), ("cheb_lo", float("nan")),
+                                         ("theta", -0.1), ("theta", float("nan")), ("max_levels", 0),
+                                         ("max_levels", 17), ("rtol", 0.0), ("max_it", 0)])
+def test_setup_rejects_bad_options_before_device_work(L, field, value):
+    """Option validation happens on the host, before any CUDA call: a bad
+    option returns IRK_ERR_INVALID with a message and no context."""
+    from paper_2010_11377_gb300.binding import irk_default_options
+    o = irk_default_options()
+    setattr(o, field, value)
+    st, out = _setup_one_unknown(L, o)
     assert st == 1 and not out.value
     assert L.irk_last_error(None)
+
+
+def test_setup_validation_other_cases(L):
+    """A custom A~ without its matrix and a NULL row pointer are rejected on the
+    host; the default options pass validation (without a GPU the call then
+    fails in CUDA, with one it builds a context)."""
+    from paper_2010_11377_gb300.binding import irk_default_options
+    st, out = _setup_one_unknown(L, irk_default_options(kind="CUSTOM"))
+    assert st == 1 and not out.value
+    st, out = _setup_one_unknown(L, irk_default_options(), null_rowptr=True)
+    assert st == 1 and not out.value
+    st, out = _setup_one_unknown(L, irk_default_options())
+    assert st != 1, L.irk_last_error(None)
+    if out.value:
+        L.irk_destroy(out)
 
 
 @pytest.mark.parametrize("N", [3, 10])
