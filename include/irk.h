@@ -326,9 +326,10 @@ irk_status irk_apply_operator(irk_ctx* ctx, const double* d_z, double* d_w, int3
  * is FP64.  Single-float pair arithmetic: each FP64 entry of M, F and h_t A is
  * split into two floats, products are exact up to the split (2^-48 relative),
  * sums carry their rounding errors, so |w - A z| is about 2^-47 times the sum
- * of the absolute terms of each row (FP64: 2^-53).  When the environment sets
- * IRK_KRON_FF=0, or an entry of M, F or h_t A lies outside [2^-64, 2^64], the
- * product is taken in FP64 on the widened z instead. */
+ * of the absolute terms of each row (FP64: 2^-53).  When the context has FP64
+ * AMG, the environment sets IRK_KRON_FF=0, or an entry of M, F or h_t A lies
+ * outside [2^-64, 2^64], the product is taken in FP64 on the widened z instead.
+ * transpose as for irk_apply_operator; both pointers device, caller-owned. */
 irk_status irk_apply_operator_f32(irk_ctx* ctx, const float* d_z, double* d_w, int32_t transpose);
 
 /* d_z = P^{-1} d_v by the substitutions of Section 4.2, one V-cycle per
