@@ -20,10 +20,12 @@ reading fixed in the design notes, step by step:
              neighbour of largest priority (phase 2).  Aggregates are
              numbered by increasing root index.
   P          tentative piecewise constant P_t (entries 1), smoothed by
-             p_smooth damped-Jacobi steps (default 2) on levels whose matrix
-             has at most 80 entries per row on average, one step on denser
-             levels: P = (I - omega D^{-1} A)^steps P_t, omega = 4 / (3 rho),
-             rho = max_i sum_j |a_ij| / |a_ii|.
+             p_smooth damped-Jacobi steps (default 2) on every level:
+             P = (I - omega D^{-1} A)^steps P_t, omega = 4 / (3 rho), rho the
+             estimate of the spectral radius of D^{-1} A by 20 steps of the
+             power iteration on the similar S = |D|^{-1/2} A |D|^{-1/2} from
+             the +-1 vector x_i = +1 iff fmix32(i ^ 0x68E31DA4) is odd:
+             x <- S x / ||x||, rho = ||S x_19|| / ||x_19||.
   coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max (2048) or
              coarsening stalls (the next level would keep more than 90% of the
              rows); the coarsest level is solved directly (dense LU) when it
@@ -140,12 +142,45 @@ def aggregate(G: sp.csr_matrix, level: int):
     return agg, root
 
 
+POWER_SALT = 0x68E31DA4
+POWER_STEPS = 20
+
+
+def power_start_vector(n: int) -> np.ndarray:
+    """The +-1 start vector of the power iteration: +1 where the MurmurHash3
+    finaliser of i ^ POWER_SALT is odd, else -1."""
+    x = (np.arange(n, dtype=np.uint64) ^ np.uint64(POWER_SALT)) & np.uint64(M32)
+    x ^= x >> np.uint64(16)
+    x = (x * np.uint64(0x85EBCA6B)) & np.uint64(M32)
+    x ^= x >> np.uint64(13)
+    x = (x * np.uint64(0xC2B2AE35)) & np.uint64(M32)
+    x ^= x >> np.uint64(16)
+    return np.where((x & np.uint64(1)) == 1, 1.0, -1.0)
+
+
+def spectral_radius_estimate(A: sp.csr_matrix, steps: int = POWER_STEPS) -> float:
+    """Estimate of rho(D^{-1} A) (D = diag A): the power iteration on the
+    similar matrix S = |D|^{-1/2} A |D|^{-1/2}, normalising every step,
+    x_{k+1} = S x_k / ||x_k||_2; returns ||S x_{steps-1}|| / ||x_{steps-1}||.
+    For symmetric A this never exceeds rho and rises with ``steps``."""
+    d = np.sqrt(np.abs(A.diagonal()))
+    x = power_start_vector(A.shape[0])
+    nx = np.linalg.norm(x)
+    ny = 0.0
+    for _ in range(steps):
+        y = (A @ ((x / nx) / d)) / d
+        ny = np.linalg.norm(y)
+        x, nx = y, ny
+    return float(ny)
+
+
 def smoothed_prolongator(A: sp.csr_matrix, agg: np.ndarray, nc: int, steps: int = 2):
-    """P = (I - omega D^{-1} A)^steps P_t, one damped-Jacobi step at a time."""
+    """P = (I - omega D^{-1} A)^steps P_t, one damped-Jacobi step at a time,
+    omega = 4 / (3 rho) with rho the power-iteration estimate of rho(D^{-1} A)."""
     n = A.shape[0]
     Pt = sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, nc))
     diag = A.diagonal()
-    rho = np.max(np.asarray(abs(A).sum(axis=1)).ravel() / np.abs(diag))
+    rho = spectral_radius_estimate(A)
     omega = 4.0 / (3.0 * rho)
     Dinv = sp.diags(1.0 / diag)
     P = Pt
@@ -198,10 +233,7 @@ class Hierarchy:
             nc = int(agg.max()) + 1
             if 10 * nc > 9 * lev.n:
                 break
-            # the extra smoothing step widens P and the coarse operator; it is
-            # taken only on levels with at most 80 entries per row on average
-            steps = p_smooth if lev.A.nnz <= 80 * lev.n else 1
-            P, _ = smoothed_prolongator(lev.A, agg, nc, steps)
+            P, _ = smoothed_prolongator(lev.A, agg, nc, p_smooth)
             lev.P = P
             lev.R = P.T.tocsr()
             lev.agg = agg

@@ -124,7 +124,7 @@ def test_vcycle_linear_and_convergent():
     for _ in range(8):
         x = x + H.vcycle(b1 - A @ x)
     rate = (np.linalg.norm(b1 - A @ x) / r0) ** (1 / 8)
-    assert rate < 0.5, rate
+    assert rate < 0.3, rate
 
 
 def test_vcycle_nonsymmetric_block():
@@ -157,8 +157,62 @@ def test_prolongator_is_jacobi_power(steps):
     Pt[np.arange(A.shape[0]), agg] = 1.0
     ref = np.linalg.matrix_power(S, steps) @ Pt
     assert np.abs(P.toarray() - ref).max() <= 1e-14
-    rho = np.max(np.abs(Ad).sum(axis=1) / np.abs(np.diag(Ad)))
-    assert omega == 4.0 / (3.0 * rho)
+    assert omega == 4.0 / (3.0 * amg.spectral_radius_estimate(A))
+    # the estimate is a lower bound of rho(D^{-1} A) for this symmetric block,
+    # within 3 % after 20 steps
+    rho = np.max(np.abs(np.linalg.eigvals(Ad / np.diag(Ad)[:, None])))
+    assert 0.97 * rho <= 4.0 / (3.0 * omega) <= rho * (1 + 1e-12)
+
+
+def test_power_start_vector():
+    """+-1 entries from the lowest bit of fmix32(i ^ 0x68E31DA4), balanced."""
+    x = amg.power_start_vector(4096)
+    assert set(np.unique(x)) == {-1.0, 1.0}
+    ref = np.array([1.0 if amg.fmix32(i ^ 0x68E31DA4) & 1 else -1.0 for i in range(4096)])
+    assert np.array_equal(x, ref)
+    assert abs(x.sum()) < 4 * np.sqrt(4096)
+
+
+def test_spectral_radius_estimate_closed_forms():
+    """The power-iteration estimate of rho(D^{-1} A) against closed forms:
+    the 1-D Laplacian tridiag(-1, 2, -1) of size n has rho(D^{-1} A) =
+    1 + cos(pi/(n+1)); a scaled diagonal matrix has D^{-1} A = I; a 2x2 block
+    with a large diagonal spread has rho = 1 + |b|/sqrt(a c), which the
+    unscaled norm ratio ||D^{-1} A x|| / ||x|| overshoots and the symmetric
+    scaling does not."""
+    for n in (6, 12):
+        T = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+        rho = 1 + np.cos(np.pi / (n + 1))
+        est = amg.spectral_radius_estimate(T)
+        assert est <= rho * (1 + 1e-14)
+        assert est >= rho * (1 - 1e-2)
+        assert abs(amg.spectral_radius_estimate(T, steps=400) - rho) < 1e-12
+    Dm = sp.diags(np.linspace(1.0, 50.0, 9)).tocsr()
+    assert abs(amg.spectral_radius_estimate(Dm) - 1.0) < 1e-15
+    a, bb, c = 100.0, -1.0, 0.01
+    B = sp.csr_matrix(np.array([[a, bb], [bb, c]]))
+    rho = 1 + abs(bb) / np.sqrt(a * c)
+    assert abs(amg.spectral_radius_estimate(B, steps=60) - rho) < 1e-12
+    x = np.array([1.0, 1.0])
+    assert np.linalg.norm((B @ x) / B.diagonal()) / np.linalg.norm(x) > 1.5 * rho
+
+
+@pytest.mark.parametrize("N", [64, 128])
+@pytest.mark.parametrize("c", [0.05 * 0.4, (1 / 64) * 0.2628])
+def test_vcycle_contraction_below_0_3(N, c):
+    """Stationary contraction of the default V-cycle on heat blocks
+    M + c K at two mesh sizes and two block coefficients (C1's and the
+    s = 5 LD block of the C2 runs): below 0.3 in the energy norm, measured by
+    the power iteration on the error propagator I - B A."""
+    A = _block(N, c=c)
+    H = amg.Hierarchy(A)
+    e = np.random.default_rng(5).standard_normal(A.shape[0])
+    rate = 0.0
+    for _ in range(20):
+        e2 = e - H.vcycle(A @ e)
+        rate = np.sqrt(e2 @ (A @ e2) / (e @ (A @ e)))
+        e = e2 / np.linalg.norm(e2)
+    assert rate < 0.3, rate
 
 
 def test_strength_on_negative_couplings():

@@ -178,6 +178,9 @@ def test_fgmres_direct_subsolve_counts_c1():
         its[kind] = sol.step(synth.heat_u0(mesh)).iterations
     assert its["J"] > its["GSL"] >= its["LD"]
     assert its["J"] > its["DU"] >= its["LD"]
+    # counts of an independent dense stage solve per step with exact subsolves
+    # (C1: 32^2, s = 2, h = 0.05, right GMRES to 1e-10)
+    assert its == {"J": 14, "GSL": 7, "DU": 6, "LD": 5}
     direct = irk.IRKSolver(prob, A, b, 0.05, kind=None).step(synth.heat_u0(mesh), direct=True).u
     sol = irk.IRKSolver(prob, A, b, 0.05, kind="LD", subsolve="amg")
     st = sol.step(synth.heat_u0(mesh))
@@ -320,3 +323,21 @@ def test_table6_lobatto_small_sizes_with_exact_subsolves():
                 its = sol.solve_stages(rhs).iterations
                 paper = ref["iterations"][str(N)][str(s)][q]
                 assert abs(its - paper) <= max(3, int(np.ceil(0.1 * paper))), (N, s, kind, its, paper)
+
+
+def test_c1_spectrum_and_final_state():
+    """C1 (heat 32^2, Radau IIA s = 2, h = 0.05, 20 steps): the smallest
+    generalised eigenvalue of (F, M) is 19.7868 (the P1 approximation of
+    2 pi^2 = 19.7392 from above), and the state after 20 direct steps has
+    ||u_20||_2 = 3.267e-8; both values come from an independent dense
+    computation of the same discretisation."""
+    mesh, prob = _heat(32)
+    lam = sla.eigh(prob.F.toarray(), prob.M.toarray(), eigvals_only=True)
+    assert abs(lam[0] - 19.7868) < 5e-4
+    assert lam[0] > 2 * np.pi ** 2
+    A, b, _ = bt.radau_iia(2)
+    sol = irk.IRKSolver(prob, A, b, 0.05, kind=None)
+    u = synth.heat_u0(mesh)
+    for _ in range(20):
+        u = sol.step(u, direct=True).u
+    assert abs(np.linalg.norm(u) - 3.267e-8) < 0.001e-8
