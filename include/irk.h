@@ -110,9 +110,10 @@ typedef struct {
                             Left preconditioning needs a fixed linear P^{-1}: use FP64 AMG for
                             rtol below the AMG precision.  Forward solves only: the adjoint
                             entry points and batches reject side = 1 */
-  int32_t p_smooth;      /* damped-Jacobi steps smoothing the tentative prolongator,
-                            P = (I - omega D^{-1} A)^p_smooth P_t, 1 or 2 (default 2); the
-                            second step only on levels with at most 80 entries per row */
+  int32_t p_smooth;      /* damped-Jacobi steps smoothing the tentative prolongator on
+                            every level, P = (I - omega D^{-1} A)^p_smooth P_t, 1, 2 or 3
+                            (default 2); omega = 4/(3 rho), rho a 20-step power-iteration
+                            estimate of the spectral radius of D^{-1} A */
   int32_t strength;      /* coupling measure of the strength test (c_ij + c_ji)/2 >= theta
                             sqrt(|a_ii a_jj|): 0 = |a_ij| (default), 1 = max(-a_ij, 0);
                             the negative-only measure helps P2 heat blocks but can leave a
@@ -351,8 +352,12 @@ irk_status irk_residual_norm(irk_ctx* ctx, const double* d_k, const double* d_b,
  * receives the norm.  The partial sums use a fixed device array inside libirk
  * with one slot per 256 rows, so n (rows per stage) may be at most
  * IRK_NOALLOC_MAX_ROWS; larger n gives IRK_ERR_CAPACITY.  The array's device
- * address is looked up the first time the entry point runs on a device; make
- * that first call outside any stream capture.  Every call shares the array
+ * address is looked up the first time the entry point runs on a device and
+ * kept for the life of the process (a device reset is not supported); make
+ * that first call outside any stream capture.  Under lazy module loading that
+ * first call may load libirk's device code, which the driver allocates memory
+ * for; later calls allocate nothing.  The norm is ready on the caller's stream
+ * when the call returns (the host does not wait).  Every call shares the array
  * (its contents are those of the last call), so calls that overlap on the GPU,
  * from any context or thread, race: serialise them. */
 #define IRK_NOALLOC_MAX_ROWS 1048576

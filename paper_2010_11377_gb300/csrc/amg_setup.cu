@@ -17,7 +17,12 @@
 //   aggregates root + strong neighbours; every other node joins the
 //              aggregate of its phase-1 strong neighbour of largest priority;
 //              aggregates numbered by increasing root index
-//   P          (I - omega D^{-1} A) P_tent, omega = 4/(3 max_i sum_j|a_ij|/|a_ii|)
+//   P          (I - omega D^{-1} A)^p P_tent (p = p_smooth on every level),
+//              omega = 4/(3 rho), rho the estimate of rho(D^{-1} A) by 20 steps
+//              of the power iteration on S = |D|^{-1/2} A |D|^{-1/2} from the
+//              +-1 vector x_i = +1 iff fmix32(i ^ 0x68E31DA4) is odd:
+//              x <- S x / ||x||, rho = ||S x_19|| / ||x_19|| (deterministic
+//              block-tree reductions)
 //   coarse     A_c = P^T A P by two deterministic SpGEMMs, until n <= coarse_max (2048)
 //              or coarsening stalls (a level would keep > 90% of its rows);
 //              the coarsest level is inverted densely (Gauss-Jordan, partial
@@ -60,23 +65,75 @@ __device__ __forceinline__ double find_entry(const int* __restrict__ rp, const i
 }
 
 __global__ void k_diag(int n, const int* __restrict__ rp, const int* __restrict__ col,
-                       const double* __restrict__ val, double* __restrict__ diag,
-                       unsigned long long* __restrict__ rho_bits, int* __restrict__ bad) {
+                       const double* __restrict__ val, double* __restrict__ diag, double* __restrict__ dsq,
+                       int* __restrict__ bad) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  double d = 0.0, s = 0.0;
-  for (int k = rp[r]; k < rp[r + 1]; ++k) {
-    double v = val[k];
-    if (col[k] == r) d = v;
-    s += fabs(v);
-  }
+  double d = 0.0;
+  for (int k = rp[r]; k < rp[r + 1]; ++k)
+    if (col[k] == r) d = val[k];
   diag[r] = d;
-  if (d == 0.0) {
-    atomicExch(bad, 1);
-    return;
+  dsq[r] = sqrt(fabs(d));
+  if (d == 0.0) atomicExch(bad, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Power iteration for rho(D^{-1} A) on S = |D|^{-1/2} A |D|^{-1/2}
+// ---------------------------------------------------------------------------
+constexpr unsigned POWER_SALT = 0x68E31DA4u;
+constexpr int POWER_STEPS = 20;
+constexpr int POWER_BS = 256;
+
+__global__ void k_power_init(int n, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (fmix32(static_cast<unsigned>(i) ^ POWER_SALT) & 1u) ? 1.0 : -1.0;
+}
+
+// y = S (x * scale), scale = 1/||x||; per-block partial sums of y_i^2 (fixed tree)
+__global__ void __launch_bounds__(POWER_BS)
+k_power_step(int n, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+             const double* __restrict__ dsq, const double* __restrict__ x, const double* __restrict__ scale,
+             double* __restrict__ y, double* __restrict__ partials) {
+  __shared__ double sh[POWER_BS];
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double yr = 0.0;
+  if (r < n) {
+    const double sc = *scale;
+    double acc = 0.0;
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      int c = col[k];
+      acc = fma(val[k], (x[c] * sc) / dsq[c], acc);
+    }
+    yr = acc / dsq[r];
+    y[r] = yr;
   }
-  double q = s / fabs(d);
-  atomicMax(rho_bits, static_cast<unsigned long long>(__double_as_longlong(q)));
+  sh[threadIdx.x] = yr * yr;
+  __syncthreads();
+  for (int o = POWER_BS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// one block: the norm from the partials in a fixed order; scale = 1/norm
+__global__ void __launch_bounds__(1024)
+k_power_norm(int nparts, const double* __restrict__ partials, double* __restrict__ norm,
+             double* __restrict__ scale) {
+  __shared__ double sh[1024];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double nv = sqrt(sh[0]);
+    *norm = nv;
+    *scale = nv > 0.0 ? 1.0 / nv : 0.0;
+  }
 }
 
 // strength flags per entry and strong count per row
@@ -398,22 +455,43 @@ __global__ void k_psmooth_merge(int n, const int* __restrict__ prp, const int* _
   if (q != qe) atomicOr(bad, 1);
 }
 
+// rho(D^{-1} A) estimated by POWER_STEPS normalised power steps on S (see the
+// file header); dsq = sqrt(|diag A|)
+static double spectral_radius_estimate(const CsrD& A, const double* dsq, cudaStream_t st) {
+  const int n = A.n;
+  Tmp tmp;
+  double* x = tmp.get<double>(n);
+  double* y = tmp.get<double>(n);
+  const unsigned nbk = nb(n, POWER_BS);
+  double* partials = tmp.get<double>(nbk);
+  double* norm = tmp.get<double>(1);
+  double* scale = tmp.get<double>(1);
+  k_power_init<<<nb(n), 256, 0, st>>>(n, x);
+  const double s0 = 1.0 / std::sqrt(static_cast<double>(n));   // ||x_0|| = sqrt(n)
+  CK(cudaMemcpyAsync(scale, &s0, sizeof(double), cudaMemcpyHostToDevice, st));
+  for (int k = 0; k < POWER_STEPS; ++k) {
+    k_power_step<<<nbk, POWER_BS, 0, st>>>(n, A.rowptr, A.col, A.val, dsq, x, scale, y, partials);
+    k_power_norm<<<1, 1024, 0, st>>>(static_cast<int>(nbk), partials, norm, scale);
+    std::swap(x, y);
+  }
+  CK_LAUNCH();
+  return rd(norm, st);
+}
+
 static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R, CsrD& Ac, DevPool& pool,
                     cudaStream_t st) {
   const CsrD& A = lev.A;
   int n = A.n;
   Tmp tmp;
   double* diag = tmp.get<double>(n);
-  unsigned long long* rho_bits = tmp.get<unsigned long long>(1);
+  double* dsq = tmp.get<double>(n);
   int* bad = tmp.get<int>(1);
-  CK(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
-  k_diag<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, rho_bits, bad);
+  k_diag<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, dsq, bad);
   CK_LAUNCH();
   if (rd(bad, st)) fail(IRK_ERR_ZERO_PIVOT, "AMG level matrix has a zero diagonal entry");
-  unsigned long long rb = rd(rho_bits, st);
-  double rho;
-  std::memcpy(&rho, &rb, sizeof(double));
+  const double rho = spectral_radius_estimate(A, dsq, st);
+  if (!(rho > 0.0) || !std::isfinite(rho)) fail(IRK_ERR_NONFINITE, "AMG spectral radius estimate is not positive");
   double omega = 4.0 / (3.0 * rho);
 
   // strength graph (threshold halved while more than n/4 nodes are isolated)
@@ -484,9 +562,8 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
   P.val = pool.get<double>(P.nnz);
   k_prolong_fill<<<nb(n), 256, 0, st>>>(n, A.rowptr, A.col, A.val, diag, lev.agg, omega, P.rowptr, P.col,
                                         P.val);
-  // further Jacobi steps: P <- P - omega D^{-1} (A P), on levels with at most
-  // 80 entries per row on average (the step widens P and the coarse operator)
-  const int steps = (A.nnz <= 80LL * n) ? p.p_smooth : 1;
+  // further Jacobi steps: P <- P - omega D^{-1} (A P)
+  const int steps = p.p_smooth;
   for (int q = 1; q < steps; ++q) {
     CK_LAUNCH();
     CsrD AP1;

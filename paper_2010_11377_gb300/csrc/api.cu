@@ -457,7 +457,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (!(o.reorth_eta >= 0.0 && o.reorth_eta < 1.0) || o.reorth < 0 || o.reorth > 1)
     return set_err(nullptr, IRK_ERR_INVALID, "reorth must be 0 or 1 and 0 <= reorth_eta < 1");
   if (o.side != 0 && o.side != 1) return set_err(nullptr, IRK_ERR_INVALID, "side must be 0 (right) or 1 (left)");
-  if (o.p_smooth < 1 || o.p_smooth > 2) return set_err(nullptr, IRK_ERR_INVALID, "p_smooth must be 1 or 2");
+  if (o.p_smooth < 1 || o.p_smooth > 3) return set_err(nullptr, IRK_ERR_INVALID, "p_smooth must be 1, 2 or 3");
   if (o.strength != 0 && o.strength != 1) return set_err(nullptr, IRK_ERR_INVALID, "strength must be 0 or 1");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
     return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..2048");
@@ -466,10 +466,16 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (M.n != F.n || M.nnz != F.nnz || M.n < 1) return set_err(nullptr, IRK_ERR_INVALID, "M and F differ in size");
   if (!M.rowptr || !F.rowptr || M.nnz < 0 || (M.nnz > 0 && (!M.col || !F.col || !M.val || !F.val)))
     return set_err(nullptr, IRK_ERR_INVALID, "bad CSR matrix");
-  for (int i = 0; i <= M.n; ++i)
+  if (M.rowptr[0] != 0 || M.rowptr[M.n] != M.nnz)
+    return set_err(nullptr, IRK_ERR_INVALID, "CSR rowptr must start at 0 and end at nnz");
+  for (int i = 0; i <= M.n; ++i) {
     if (M.rowptr[i] != F.rowptr[i]) return set_err(nullptr, IRK_ERR_INVALID, "M and F must share one pattern");
-  for (int64_t k = 0; k < M.nnz; ++k)
+    if (i > 0 && M.rowptr[i] < M.rowptr[i - 1]) return set_err(nullptr, IRK_ERR_INVALID, "CSR rowptr not monotone");
+  }
+  for (int64_t k = 0; k < M.nnz; ++k) {
     if (M.col[k] != F.col[k]) return set_err(nullptr, IRK_ERR_INVALID, "M and F must share one pattern");
+    if (M.col[k] < 0 || M.col[k] >= M.n) return set_err(nullptr, IRK_ERR_INVALID, "CSR column index out of range");
+  }
   if (prob->n_tri > 0 && (!prob->xy || !prob->tri || !prob->dof || prob->n_nodes <= 0))
     return set_err(nullptr, IRK_ERR_INVALID, "incomplete mesh");
 

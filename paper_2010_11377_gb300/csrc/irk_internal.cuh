@@ -449,6 +449,8 @@ void adjoint_grad_launch_at(Ctx& c, const double* u_base, const double* k_base, 
 void assemble_kappa_launch(Ctx& c, const double* kappa, double* Fval, cudaStream_t st);
 void convert_launch(const void* in, int in_prec, void* out, int out_prec, int64_t n, cudaStream_t st);
 void profile_kron_launch(Ctx& c, cudaStream_t st);
+// threads (= rows per grid-stride pass) per block of the outer Krylov kernels
+constexpr int OUTER_BLOCK = 256;
 void residual_norm_launch(Ctx& c, const double* k, const double* b, double* partials, int grid, double* out,
                           cudaStream_t st);
 void profile_gs_launch(Ctx& c, GmresState* scratch, bool axpy, cudaStream_t st);

@@ -18,7 +18,7 @@
 namespace irk {
 
 constexpr int PL = MAX_M + 2;   // partial-sum slots per block
-constexpr int BS = 256;         // threads per block of the outer kernels
+constexpr int BS = OUTER_BLOCK;   // threads per block of the outer kernels
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 

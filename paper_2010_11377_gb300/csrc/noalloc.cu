@@ -11,15 +11,21 @@
 // limited to IRK_NOALLOC_MAX_ROWS rows.  Host code cannot use the array's
 // name as a device address (it is a host-side stand-in), so its address is
 // looked up with cudaGetSymbolAddress once per device, with that device
-// current, the first time the entry point runs on it.
+// current, the first time the entry point runs on it, and kept for the life
+// of the process (a device reset that drops libirk's module is not supported).
+// Under lazy module loading that first lookup may load the module, which the
+// CUDA driver allocates memory for; later calls allocate nothing.
 #include "irk_internal.cuh"
 
+#include <exception>
 #include <mutex>
+#include <new>
 #include <string>
 
 namespace {
 
-constexpr int kBlockRows = 256;                       // rows per block of k_resid_partials
+constexpr int kBlockRows = irk::OUTER_BLOCK;       // rows per block of the residual kernel
+static_assert(kBlockRows == 256, "one scratch slot per 256-row block");
 constexpr int kMaxBlocks = IRK_NOALLOC_MAX_ROWS / kBlockRows;
 
 static __device__ __align__(256) double g_resid_scratch[kMaxBlocks];
@@ -48,25 +54,27 @@ irk_status scratch_address(int dev, double** out, std::string& err) {
   return IRK_OK;
 }
 
+irk_status fail_with(irk::Ctx* c, irk_status st, const std::string& msg) {
+  irk::set_global_error(msg);
+  if (c) c->err = msg;
+  return st;
+}
+
 }  // namespace
 
 extern "C" irk_status irk_residual_norm_noalloc(irk_ctx* h, const double* d_k, const double* d_b, double* d_norm) {
-  if (!h || !d_k || !d_b || !d_norm) {
-    irk::set_global_error("NULL argument");
-    if (h) h->c.err = "NULL argument";
-    return IRK_ERR_INVALID;
-  }
+  if (!h || !d_k || !d_b || !d_norm) return fail_with(h ? &h->c : nullptr, IRK_ERR_INVALID, "NULL argument");
   irk::Ctx& c = h->c;
-  if (c.n > IRK_NOALLOC_MAX_ROWS) {
-    c.err = "irk_residual_norm_noalloc: n = " + std::to_string(c.n) + " rows per stage exceeds the maximum of " +
-            std::to_string(IRK_NOALLOC_MAX_ROWS);
-    return IRK_ERR_CAPACITY;
-  }
   try {
+    if (c.n > IRK_NOALLOC_MAX_ROWS)
+      return fail_with(&c, IRK_ERR_CAPACITY,
+                       "irk_residual_norm_noalloc: n = " + std::to_string(c.n) +
+                           " rows per stage exceeds the maximum of " + std::to_string(IRK_NOALLOC_MAX_ROWS));
     CK(cudaSetDevice(c.device));
     double* scratch = nullptr;
-    irk_status st = scratch_address(c.device, &scratch, c.err);
-    if (st != IRK_OK) return st;
+    std::string err;
+    irk_status st = scratch_address(c.device, &scratch, err);
+    if (st != IRK_OK) return fail_with(&c, st, err);
     CK(cudaEventRecord(c.ev_a, c.user_stream));
     CK(cudaStreamWaitEvent(c.stream, c.ev_a, 0));
     // every slot that the final sum reads is written by its block first: nothing
@@ -74,12 +82,15 @@ extern "C" irk_status irk_residual_norm_noalloc(irk_ctx* h, const double* d_k, c
     int grid = (c.n + kBlockRows - 1) / kBlockRows;
     irk::residual_norm_launch(c, d_k, d_b, scratch, grid, d_norm, c.stream);
     c.launches += 2;
+    // the caller's stream waits for the norm; the host does not
     CK(cudaEventRecord(c.ev_b, c.stream));
     CK(cudaStreamWaitEvent(c.user_stream, c.ev_b, 0));
-    CK(cudaStreamSynchronize(c.stream));
   } catch (const irk::Error& e) {
-    c.err = e.msg;
-    return e.st;
+    return fail_with(&c, e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail_with(&c, IRK_ERR_NOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail_with(&c, IRK_ERR_INVALID, e.what());
   }
   return IRK_OK;
 }

@@ -168,7 +168,7 @@ def _setup_one_unknown(L, o, null_rowptr=False):
 
 
 @pytest.mark.parametrize("field,value", [("reorth_eta", 1.0), ("reorth_eta", -0.1), ("reorth", 2),
-                                         ("restart", 0), ("coarse_max", 4096), ("cheb_degree", 0), ("p_smooth", 0), ("strength", 2),
+                                         ("restart", 0), ("coarse_max", 4096), ("cheb_degree", 0), ("p_smooth", 0), ("p_smooth", 4), ("strength", 2),
                                          ("side", 2), ("kind", 6), ("kind", -1), ("smoother", 2),
                                          ("cheb_lo", 0.0), ("cheb_lo", 1.0), ("cheb_lo", float("nan")),
                                          ("theta", -0.1), ("theta", float("nan")), ("max_levels", 0),
@@ -197,6 +197,43 @@ def test_setup_validation_other_cases(L):
     assert st != 1, L.irk_last_error(None)
     if out.value:
         L.irk_destroy(out)
+
+
+def _setup_csr(L, n, nnz, rowptr, col):
+    """irk_setup on a CSR structure given as Python lists (values all one)."""
+    import ctypes as C
+    from paper_2010_11377_gb300 import _abi as A
+    from paper_2010_11377_gb300.binding import irk_default_options
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ones(max(len(col), 1))
+    Am, b, c = (np.ascontiguousarray(x, dtype=np.float64) for x in obt.radau_iia(2))
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    prob = A.IrkProblem()
+    prob.M = A.IrkCsr(n, nnz, rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                      cl.ctypes.data_as(C.POINTER(C.c_int32)), dp(val))
+    prob.F = prob.M
+    bt = A.IrkButcher(2, dp(Am), dp(b), dp(c))
+    out = C.c_void_p()
+    o = irk_default_options()
+    st = L.irk_setup(C.byref(prob), C.byref(bt), 0.1, C.byref(o), None, C.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("rowptr,col,why", [
+    ([1, 2, 3], [0, 1, 1], "rowptr[0] != 0"),
+    ([0, 2, 2], [0, 1, 1], "rowptr[n] != nnz"),
+    ([0, 3, 2], [0, 1, 1], "rowptr decreasing"),
+    ([0, 1, 3], [0, 0, 2], "column n"),
+    ([0, 1, 3], [0, -1, 1], "negative column"),
+])
+def test_setup_rejects_malformed_csr_before_device_work(L, rowptr, col, why):
+    """A CSR structure whose row pointer does not start at 0, end at nnz and
+    rise monotonically, or whose columns leave [0, n), is rejected on the host
+    with IRK_ERR_INVALID before any device work (no context is made)."""
+    st, out = _setup_csr(L, 2, 3, rowptr, col)
+    assert st == 1 and not out.value, why
+    assert L.irk_last_error(None)
 
 
 @pytest.mark.parametrize("N", [3, 10])

@@ -149,7 +149,7 @@ def test_operator_f32_range_fallback():
 
 
 @pytest.mark.parametrize("which", ["heat", "dg"])
-@pytest.mark.parametrize("p_smooth,strength", [(1, 0), (2, 1), (2, 0)])
+@pytest.mark.parametrize("p_smooth,strength", [(1, 0), (2, 1), (2, 0), (3, 0)])
 def test_aggregates_and_galerkin_parity(which, p_smooth, strength):
     mesh, prob = heat(57) if which == "heat" else dg(57)
     A, _, _ = obt.radau_iia(3)

@@ -39,6 +39,16 @@ def test_noalloc_matches_scratch_entry_point(B):
         B.irk_residual_norm_noalloc(ctx, k, rhs, out)
         got = float(out.item())
         assert abs(got - ref) <= 1e-13 * ref, (seed, got, ref)
+    # after the first call on the device, a call changes neither the device's
+    # free memory nor the caching allocator's allocation count
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    B.irk_residual_norm_noalloc(ctx, k, rhs, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
+    assert abs(float(out.item()) - ref) <= 1e-13 * ref
     ctx.close()
 
 
