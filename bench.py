@@ -174,12 +174,52 @@ def e2e_steps(ctx, u_host, steps):
     return e0.elapsed_time(e1), 8 * n, 8 * n
 
 
+def read_traffic(path):
+    """'name: value' lines of the ncu summary file (values in bytes or ms; 'null' = none)."""
+    out = {}
+    if path and os.path.exists(path):
+        for ln in open(path):
+            if ln.startswith("#") or ":" not in ln:
+                continue
+            k, v = ln.split(":", 1)
+            v = v.strip()
+            out[k.strip()] = None if v == "null" else float(v)
+    return out
+
+
+def step_roofline(ctx, prof, its_per_step, ms_per_step, hbm, recorded):
+    """Algorithmic bytes of one time step: per FGMRES iteration the
+    preconditioner (sweeps + V-cycles, its own accounting) and the operator,
+    plus both Gram-Schmidt passes at the iteration's basis index j (linear in
+    j: taken from the library's accounting at j = 0 and 1); the per-solve
+    kernels (right-hand side, true residual, solution and stage update, about
+    1 % of the bytes) are not counted.  Achieved = bytes / measured time per
+    step (the timed steps' CUDA events)."""
+    from paper_2010_11377_gb300 import binding as B
+    gs = {}
+    for k in ("gs_dots", "gs_axpy"):
+        b0 = B.irk_profile(ctx, k, j=0, warm=0, reps=1)["bytes"]
+        b1 = B.irk_profile(ctx, k, j=1, warm=0, reps=1)["bytes"]
+        gs[k] = (b0, b1 - b0)
+    nit = max(1, int(round(its_per_step)))
+    jsum = sum(i % 30 for i in range(nit)) * its_per_step / nit
+    per_it = prof["precond"]["bytes"] + prof["kron"]["bytes"] + gs["gs_dots"][0] + gs["gs_axpy"][0]
+    total = its_per_step * per_it + (gs["gs_dots"][1] + gs["gs_axpy"][1]) * jsum
+    gbps = total / (ms_per_step * 1e-3) / 1e9
+    traffic = recorded.get("step traffic_bytes_per_step")
+    return {"bound": "hbm", "achieved": gbps, "peak": hbm, "unit": "GB/s", "frac": gbps / hbm,
+            "bytes_per_step": total, "ms_per_step": ms_per_step,
+            "counted": "per iteration: preconditioner, operator, both Gram-Schmidt passes; per-solve kernels not counted",
+            "traffic_per_step": traffic,
+            "traffic_over_algorithmic": (traffic / total) if traffic else None}
+
+
 # FP64 FMA throughput measured on this pool's GB300 (independent FMA chains,
 # 152 SMs at ~1987 MHz): 1.196 TFLOP/s; nominal 1.25 TFLOP/s at 2070 MHz.
 FP64_TFLOPS = 1.196
 
 
-def roofline(ctx, s, its_per_step, traffic_file):
+def roofline(ctx, s, its_per_step, ms_per_step, traffic_file):
     """Per-kernel timing (CUDA events on the library stream, standalone
     replays on the buffers of the last solve).  The finest-level smoothing
     step carries the largest share of a step's time (ncu launch lists); it is
@@ -198,17 +238,18 @@ def roofline(ctx, s, its_per_step, traffic_file):
         r["GBps"] = r["bytes"] / (r["ms"] * 1e-3) / 1e9
         r["TFLOPs"] = r["flops"] / (r["ms"] * 1e-3) / 1e12
         prof[tgt] = r
-    traffic = None
-    if traffic_file and os.path.exists(traffic_file):
-        for ln in open(traffic_file):
-            if ln.startswith("k_smooth_level0 traffic_bytes_per_launch:"):
-                v = ln.split(":", 1)[1].strip()
-                traffic = None if v == "null" else float(v)
+    recorded = read_traffic(traffic_file)
     t = prof["smooth0"]
     roof = {"bound": "hbm", "achieved": t["GBps"], "peak": hbm, "unit": "GB/s", "frac": t["GBps"] / hbm,
-            "traffic": traffic, "kernel": "k_smooth (finest level, one Chebyshev step)",
+            "traffic": recorded.get("k_smooth_level0 traffic_bytes_per_launch"),
+            "kernel": "k_smooth (finest level, one Chebyshev step)",
             "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst",
-            "algorithmic_bytes_per_launch": t["bytes"], "ms_per_launch": t["ms"]}
+            "algorithmic_bytes_per_launch": t["bytes"], "ms_per_launch": t["ms"],
+            "timing": "mean of 20 warm back-to-back replays of one launch (CUDA events, library stream)",
+            "ncu_cold_ms_per_launch": recorded.get("k_smooth_level0 cold_ms_per_launch")}
+    # the whole solve: algorithmic bytes of one time step's iteration kernels
+    # (library accounting) over the measured time per step
+    roof["step"] = step_roofline(ctx, prof, its_per_step, ms_per_step, hbm, recorded)
     fp64 = {}
     for k in ("gs_dots", "gs_axpy"):
         r = prof[k]
@@ -252,9 +293,18 @@ class OracleSample:
         self.pc = oirk.BlockPreconditioner(prob.M, prob.F, A, h, kind, "amg")
         self.setup_s = time.perf_counter() - t0
         self.n = mesh.n
-        self.rhs = oirk.stage_rhs(prob.F, prob.g, synth.heat_u0(mesh), s)
+        self.u0 = synth.heat_u0(mesh)
+        self.rhs = oirk.stage_rhs(prob.F, prob.g, self.u0, s)
         self.op = lambda z: oirk.apply_operator(prob.M, prob.F, A, h, z)  # noqa: E731
         self.fgmres = oirk.fgmres
+        self._stage_rhs = lambda u: oirk.stage_rhs(prob.F, prob.g, u, s)  # noqa: E731
+        self.b, self.h = b, h
+
+    def step(self, u):
+        """One whole oracle time step from u: stage right-hand side, the
+        preconditioned FGMRES solve, u + h sum_i b_i k_i.  Returns (u, its)."""
+        res = self.fgmres(self.op, self.pc.apply, self._stage_rhs(u))
+        return u + self.h * (self.b @ res.x), res.iterations
 
     def full_step_iterations(self):
         return self.fgmres(self.op, self.pc.apply, self.rhs).iterations
@@ -275,15 +325,35 @@ def host_threads():
         return 1
 
 
-def cpu_baseline(name, iterations_per_step, budget_s=20.0):
+def thread_limit(n):
+    """Context limiting the BLAS/OpenMP pools to n threads (threadpoolctl when
+    present; the oracle's sparse products are single-threaded either way)."""
+    try:
+        import threadpoolctl
+        return threadpoolctl.threadpool_limits(n)
+    except Exception:
+        import contextlib
+        return contextlib.nullcontext()
+
+
+def cpu_baseline(name, iterations_per_step, budget_s=12.0):
+    """The oracle on this host: a bounded sample of FGMRES iterations of one
+    time step, scaled to the step's iteration count, with the BLAS pool at
+    every host core and again at one thread."""
+    nproc = os.cpu_count() or 1
     o = OracleSample(name)
     _, t1 = o.sample(1, iterations_per_step)
     k = int(max(1, min(iterations_per_step, budget_s // max(t1, 1e-3))))
-    value, per_it = o.sample(k, iterations_per_step)
-    return {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+    with thread_limit(nproc):
+        value, per_it = o.sample(k, iterations_per_step)
+    with thread_limit(1):
+        value1, per_it1 = o.sample(k, iterations_per_step)
+    return {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
             "sample": f"{name}: {k} FGMRES iterations of one time step (AMG setup {o.setup_s:.1f} s untimed), "
-                      f"per-iteration time x {iterations_per_step} iterations per step (the GPU run's count)",
-            "seconds_per_iteration": per_it}
+                      f"per-iteration time x {iterations_per_step} iterations per step (the GPU run's count); "
+                      f"BLAS pool at {nproc} threads (the sparse products run on one)",
+            "seconds_per_iteration": per_it, "host_cores": nproc,
+            "one_thread": {"value": value1, "seconds_per_iteration": per_it1}}
 
 
 def aggregate_ranks(ms, units, dist=None, device=None):
@@ -342,8 +412,12 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded P1 heat problem; u0 = sin(pi x) sin(pi y))",
         "config": {"workload": name, "grid": f"{N}x{N}", "n_per_stage": n, "stages": s, "method": "Radau IIA",
-                   "h_t": h, "precond": f"P_{kind}", "amg": prec + " SA V-cycle (prolongator smoothed twice, Chebyshev 4, V(1,1), coarsest <= 2048 rows)",
+                   "h_t": h, "precond": f"P_{kind}", "amg": prec + " SA V-cycle (prolongator smoothed twice with omega from a power-iteration rho(D^-1 A), "
+                                 "Chebyshev 4, V(1,1), coarsest <= 2048 rows)",
                    "krylov": "FGMRES(30) rtol 1e-10", "parallelism": f"replicas x{world}",
+                   "operator": "FP64 M and F times the FP32 preconditioner outputs in single-float pairs "
+                               "(about 2^-47 of each row's absolute terms); the true residual, Gram-Schmidt "
+                               "and the updates in FP64",
                    "l2": "working set > L2 (Krylov bases 1.3 GB); no flush"},
         "iterations_per_step": its, "resid": st["resid"], "setup_s": setup_s,
         "device_mem_gb": round(device_mem_gb, 2),
@@ -358,7 +432,7 @@ def run_ours(args):
     out["e2e"] = {"value": s * n * e2e_steps_n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                   "d2h_bytes_per_step": bo}
     # roofline of the dominant kernel
-    roof, extra = roofline(ctx, s, its, os.path.join(ROOT, "profiles", "ncu_traffic.txt"))
+    roof, extra = roofline(ctx, s, its, ms / args.steps, os.path.join(ROOT, "profiles", "ncu_traffic.txt"))
     out["roofline"] = roof
     out["kernels"] = extra
     # FP64-AMG form of the same workload (the FP32-AMG speedup at equal accuracy)
@@ -370,6 +444,12 @@ def run_ours(args):
         out["fp64_amg"] = {"ms_per_step": ms64 / k64, "iterations_per_step": st64["iterations"] / k64,
                            "speedup_of_f32_amg": (ms64 / k64) / (ms / args.steps), "resid": st64["resid"]}
         ctx64.close()
+    # the batched adjoint workload on a subset of 8 instances (64^2 .. 512^2)
+    if not args.no_batch:
+        bf = batch_figures(8, 1)
+        out["batch8"] = {k: bf[k] for k in ("value", "unit", "forward_ms", "adjoint_ms", "adjoint_over_forward",
+                                            "mean_iterations_per_instance_run", "setup_s")}
+        out["batch8"]["config"] = bf["config"]
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(name, max(1, int(round(its))))
     print(json.dumps(out))
@@ -410,6 +490,8 @@ def run_sweep(args):
       t6  as t5 with Lobatto IIIC, s = 2..5, h_t = h_x^(3/(2s-2)) (the paper's Table 6)
       t8  as t5 with left-preconditioned GMRES (preconditioned residual), FP64 AMG, and the
           optimised GSL too (the setting of the paper's Table 8)
+      t9  as t8 with Lobatto IIIC, s = 2..4, h_t = h_x^(3/(2s-2)) (the paper's Table 9)
+      t13 as t12 at h_x^-1 = 128 with h_t in {0.05, 0.1, 0.5, 1, 5}, s in {2, 7} (Table 13)
       t12 SUPG + Nitsche double glazing, h_x^-1 in {64, 128}, eps in {0.04, 0.005}, s = 2..7,
           h_t = h_x^(2/(2s-1)), manufactured b, left GMRES, FP64 AMG with Chebyshev on
           [0.3, 1] and one prolongator smoothing step, GSL / LD (Table 12)"""
@@ -522,14 +604,16 @@ def run_sweep(args):
                                       "its": st["iterations"], "ms": round(st["ms"], 3), "resid": st["resid"],
                                       "err_vs_kstar": err}), flush=True)
                     ctx.close()
-    elif args.sweep == "t8":
-        # the paper's left-preconditioned comparison (Table 8): P2 heat, manufactured b,
-        # left GMRES to 1e-8 on the preconditioned residual, FP64 AMG, all five A~
-        for s in (2, 3, 4, 5, 6):
-            A, b, c = B.irk_butcher_table("radau_iia", s)
+    elif args.sweep in ("t8", "t9"):
+        # the paper's left-preconditioned comparisons (Table 8 Radau IIA s = 2..6, Table 9
+        # Lobatto IIIC s = 2..4): P2 heat, manufactured b, left GMRES to 1e-8 on the
+        # preconditioned residual, FP64 AMG, all five A~
+        lob = args.sweep == "t9"
+        for s in ((2, 3, 4) if lob else (2, 3, 4, 5, 6)):
+            A, b, c = B.irk_butcher_table("lobatto_iiic" if lob else "radau_iia", s)
             for N in (8, 16, 32, 64, 128):
                 p = problems.heat_p2(N)
-                h = (1.0 / N) ** (3.0 / (2 * s - 1))
+                h = (1.0 / N) ** (3.0 / ((2 * s - 2) if lob else (2 * s - 1)))
                 kstar = torch.tensor(synth.random_stage_block(p["n"], s, 1000 + N).ravel(), device="cuda")
                 for kind in ("J", "GSL", "GSL_OPT", "DU", "LD"):
                     o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64",
@@ -541,7 +625,8 @@ def run_sweep(args):
                     B.irk_solve(ctx, rhs, k)
                     st = B.irk_solve(ctx, rhs, k)
                     err = float((k - kstar).norm() / kstar.norm())
-                    print(json.dumps({"sweep": "t8", "problem": "heat_p2", "N": N, "n": p["n"], "s": s,
+                    print(json.dumps({"sweep": args.sweep, "problem": "heat_p2", "N": N, "n": p["n"], "s": s,
+                                      "method": "lobatto_iiic" if lob else "radau_iia",
                                       "dof": s * p["n"], "h_t": h, "precond": kind, "strength": args.strength,
                                       "its": st["iterations"],
                                       "ms": round(st["ms"], 3), "resid": st["resid"], "err_vs_kstar": err}),
@@ -576,6 +661,33 @@ def run_sweep(args):
                                           "precond": kind, "its": st["iterations"], "ms": round(st["ms"], 3),
                                           "resid": st["resid"], "err_vs_kstar": err}), flush=True)
                         ctx.close()
+    elif args.sweep == "t13":
+        # the paper's double-glazing time-step table (Table 13): SUPG + Nitsche P1 at
+        # h_x^-1 = 128, h_t in {0.05, 0.1, 0.5, 1, 5}, s in {2, 7}, manufactured b = A k*,
+        # left-preconditioned GMRES to 1e-8, FP64 AMG as in the t12 sweep, GSL / LD
+        hinv = 128
+        for eps in (0.04, 0.005):
+            p = problems.double_glazing_supg(2 * hinv, eps)
+            for s in (2, 7):
+                A, b, c = B.irk_butcher_table("radau_iia", s)
+                kstar = torch.tensor(synth.random_stage_block(p["n"], s, 3000 + s).ravel(), device="cuda")
+                for h in (0.05, 0.1, 0.5, 1.0, 5.0):
+                    for kind in ("GSL", "LD"):
+                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", cheb_lo=0.3,
+                                                  p_smooth=1)
+                        ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o,
+                                          g=p["g"])
+                        rhs = torch.empty_like(kstar)
+                        B.irk_apply_operator(ctx, kstar, rhs)
+                        k = torch.empty_like(kstar)
+                        B.irk_solve(ctx, rhs, k)
+                        st = B.irk_solve(ctx, rhs, k)
+                        err = float((k - kstar).norm() / kstar.norm())
+                        print(json.dumps({"sweep": "t13", "problem": "double_glazing_supg", "hx_inv": hinv,
+                                          "n": p["n"], "s": s, "h_t": h, "eps": eps, "precond": kind,
+                                          "its": st["iterations"], "ms": round(st["ms"], 3),
+                                          "resid": st["resid"], "err_vs_kstar": err}), flush=True)
+                        ctx.close()
     elif args.sweep == "htlr":
         p = problems.heat(128)
         u0 = synth.heat_u0(p["mesh"])
@@ -600,15 +712,22 @@ def run_batch(args):
     s = 3, h_t = 1/32, 32 steps, checkpoints every 8; one graph launch runs
     every instance forward, one more runs the checkpointed adjoint (gradients
     of 1/2 (u_N - d)^T M (u_N - d) w.r.t. u0 and kappa)."""
+    from __graft_entry__ import build
+    build()
+    print(json.dumps(batch_figures(args.batch_count, max(1, args.steps // 4))))
+
+
+def batch_figures(count, reps):
+    """The batched workload of `count` instances (sizes geometric from 64^2 to
+    512^2): set-up seconds, the best of `reps` forward and adjoint graph
+    launches after one warm forward launch."""
     import numpy as np
     import torch
     import synth
-    from __graft_entry__ import build
-    build()
     from paper_2010_11377_gb300 import binding as B
     from paper_2010_11377_gb300 import problems
     s, h, nsteps, every = 3, 1.0 / 32, 32, 8
-    sizes = synth.batch_instance_sizes(args.batch_count)
+    sizes = synth.batch_instance_sizes(count)
     A, b, c = B.irk_butcher_table("radau_iia", s)
     ctxs, u0s, uNs, cks, lams, grads = [], [], [], [], [], []
     t0 = time.perf_counter()
@@ -630,7 +749,7 @@ def run_batch(args):
     B.irk_batch_run(batch)                    # warm
     fwd_ms = []
     adj_ms = []
-    for _ in range(max(1, args.steps // 4)):
+    for _ in range(reps):
         st, ms = B.irk_batch_run(batch)
         fwd_ms.append(ms)
         for q, ctx in enumerate(ctxs):
@@ -649,36 +768,46 @@ def run_batch(args):
            "launches": {"forward": 1, "adjoint": 1},
            "grad_norms": {"u0": float(sum(float(l.norm()) ** 2 for l in lams) ** 0.5),
                           "kappa": float(sum(float(g.norm()) ** 2 for g in grads) ** 0.5)}}
-    print(json.dumps(out))
     batch.close()
     for ctx in ctxs:
         ctx.close()
+    return out
 
 
-def run_reference(args):
+def run_reference(args, budget_s=100.0):
     """Reference arm: the FP64 oracle (the paper has no code) on the host cores,
-    same metric and workload.  Set-up and one full step (to count its FGMRES
-    iterations) are untimed; each timed step is a bounded sample of FGMRES
-    iterations scaled to that count."""
+    same metric and workload.  Set-up is untimed; after at most one untimed
+    warm-up step, whole oracle time steps are timed one by one (wall clock)
+    until K steps are done or the timed steps have used `budget_s`; the line
+    reports the steps actually timed."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
     name = args.workload
+    nproc = os.cpu_count() or 1
     o = OracleSample(name)
-    its = o.full_step_iterations()
-    per_step = []
-    k = 2
-    for i in range(args.warmup + args.steps):
-        v, _ = o.sample(k, its)
-        if i >= args.warmup:
-            per_step.append(1.0 / v)
-    value = 1.0 / (sum(per_step) / len(per_step))
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * o.s * o.n / value, "higher_is_better": True,
-           "dtype": "f64", "data": "synthetic", "config": {"workload": name},
-           "cpu_baseline": {"kind": "oracle", "cores": host_threads(), "value": value,
-                            "sample": f"{name}: each step {k} FGMRES iterations of the oracle, scaled to the "
-                                      f"{its} iterations of its full step (setup {o.setup_s:.1f} s untimed)"},
+    u = o.u0
+    warm = min(args.warmup, 1)
+    with thread_limit(nproc):
+        for _ in range(warm):
+            u, _ = o.step(u)
+        times, its = [], []
+        while len(times) < max(1, args.steps) and (not times or sum(times) < budget_s):
+            t0 = time.perf_counter()
+            u, it = o.step(u)
+            times.append(time.perf_counter() - t0)
+            its.append(it)
+    ms = 1e3 * sum(times) / len(times)
+    value = o.s * o.n / (ms * 1e-3)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(times),
+           "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (seeded P1 heat problem; u0 = sin(pi x) sin(pi y))",
+           "config": {"workload": name}, "iterations_per_step": sum(its) / len(its),
+           "steps_requested": args.steps, "warmup_requested": args.warmup,
+           "cpu_baseline": {"kind": "oracle", "cores": nproc, "value": value,
+                            "sample": f"{name}: {len(times)} whole oracle time steps after {warm} untimed "
+                                      f"(setup {o.setup_s:.1f} s untimed; timed steps stop after {budget_s:.0f} s); "
+                                      f"BLAS pool at {nproc} threads, sparse products on one"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -692,6 +821,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="leave the 8-instance batch figures out of the line")
     ap.add_argument("--batch", action="store_true", help="the batched uneven-instance workload")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--kernel", default=None,
@@ -701,14 +831,14 @@ def main():
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--strength", type=int, default=0, choices=[0, 1],
                     help="AMG strength measure for the P2 sweeps (t5 t6 t8): 0 |a_ij|, 1 max(-a_ij, 0)")
-    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t12"],
+    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t9", "t12", "t13"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--launch-list", action="store_true",
                     help="only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()
     if args.launch_list:
-        args.no_cpu_baseline = args.no_fp64 = True
+        args.no_cpu_baseline = args.no_fp64 = args.no_batch = True
     if args.impl == "reference":
         run_reference(args)
     elif args.batch:

@@ -1,0 +1,149 @@
+"""GPU steps on hierarchies of three or more levels with the library's default
+AMG options, against the oracle's exact stage solves: every precision of the
+preconditioner (FP64, FP32, BF16 finest level) and the operator with and
+without single-float pairs; and a batch of 8 uneven instances (64^2..256^2).
+
+Run as a script (``python tests/test_gpu_multilevel.py N steps``) it prints
+the per-precision errors against the oracle as one JSON line; the test of the
+FP64-product operator runs it in a child process, since that operator is
+selected once per process (environment variable IRK_KRON_FF=0)."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from oracle import butcher as obt  # noqa: E402
+from oracle import fem as ofem  # noqa: E402
+from oracle import irk as oirk  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _build():
+    from paper_2010_11377_gb300.build import build
+    build()
+    from paper_2010_11377_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return _build()
+
+
+def step_errors(B, N, nsteps, precs=("f64", "f32", "bf16"), s=5, h=1 / 64, kind="LD"):
+    """Heat N^2, Radau IIA s, P_kind, default options (FP32/FP64/BF16 AMG):
+    relative L2 error of every step's state against the oracle's exact stage
+    solves, the iteration counts and the hierarchy sizes of the first block."""
+    from paper_2010_11377_gb300 import problems
+    mesh = synth.structured_mesh(N)
+    prob = ofem.heat_problem(mesh)
+    A, b, _ = obt.radau_iia(s)
+    refs, _ = oirk.IRKSolver(prob, A, b, h, kind=None).run(synth.heat_u0(mesh), nsteps, direct=True)
+    p = problems.heat(N)
+    At, bt, ct = B.irk_butcher_table("radau_iia", s)
+    out = {}
+    for prec in precs:
+        o = B.irk_default_options(kind=kind, amg_prec=prec)
+        ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (At, bt, ct), h, options=o)
+        u = torch.tensor(refs[0], dtype=torch.float64, device="cuda")
+        errs, its = [], []
+        for t in range(nsteps):
+            nxt = torch.empty_like(u)
+            st = B.irk_step(ctx, u, nxt)
+            got = nxt.cpu().numpy()
+            errs.append(float(np.linalg.norm(got - refs[t + 1]) / np.linalg.norm(refs[t + 1])))
+            its.append(st["iterations"])
+            u = nxt
+        rows, _ = B.irk_amg_info(ctx, 0)
+        out[prec] = {"errors": errs, "iterations": its, "levels": rows}
+        ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("N", [128])
+def test_multilevel_steps_against_exact_solve(B, N):
+    """128^2 heat, s = 5, LD, default options: the finest block coarsens over
+    at least three levels, and every step in every preconditioner precision is
+    within 1e-8 of the exact stage solve."""
+    res = step_errors(B, N, 3)
+    for prec, r in res.items():
+        assert len(r["levels"]) >= 3, (prec, r["levels"])
+        assert max(r["errors"]) <= 1e-8, (prec, r)
+    # the oracle's FGMRES with the same AMG reading takes as many iterations
+    mesh = synth.structured_mesh(N)
+    prob = ofem.heat_problem(mesh)
+    A, b, _ = obt.radau_iia(5)
+    oits = oirk.IRKSolver(prob, A, b, 1 / 64, kind="LD", subsolve="amg").step(synth.heat_u0(mesh)).iterations
+    got = res["f64"]["iterations"][0]
+    assert abs(got - oits) <= max(1, int(np.ceil(0.1 * oits))), (got, oits)
+
+
+def test_operator_without_pairs_child_process(B):
+    """The FP32-AMG step with the operator in FP64 products (IRK_KRON_FF=0, a
+    child process) is within 1e-8 of the exact solve, like the pair operator."""
+    env = dict(os.environ, IRK_KRON_FF="0")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "96", "2", "f32"], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    assert max(res["f32"]["errors"]) <= 1e-8, res
+
+
+def test_batch_of_eight_64_to_256(B):
+    """8 uneven heat instances, 64^2..256^2, s = 3, h = 1/32, 8 steps,
+    checkpoints every 4: one graph launch equals the per-instance runs bit for
+    bit and the largest instance is within 1e-8 of the oracle's exact solves."""
+    from paper_2010_11377_gb300 import problems
+    s, h, nsteps, every = 3, 1 / 32, 8, 4
+    sizes = synth.batch_instance_sizes(8, 64, 256)
+    assert sizes[0] == 64 and sizes[-1] == 256
+    A, b, c = B.irk_butcher_table("radau_iia", s)
+    ctxs, u0s, uNs, cks, lams, grads, meta = [], [], [], [], [], [], []
+    for i, N in enumerate(sizes):
+        mesh = synth.structured_mesh(N)
+        kap = np.exp(synth.grf_log_kappa(mesh, seed=i))
+        p = problems.heat(N, kappa=kap)
+        ctxs.append(B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, mesh=p["mesh_arrays"]))
+        u0 = synth.random_smooth_u0(mesh, seed=i)
+        u0s.append(torch.tensor(u0, dtype=torch.float64, device="cuda"))
+        uNs.append(torch.empty(mesh.n, dtype=torch.float64, device="cuda"))
+        cks.append(torch.empty(nsteps // every, mesh.n, dtype=torch.float64, device="cuda"))
+        lams.append(torch.empty(mesh.n, dtype=torch.float64, device="cuda"))
+        grads.append(torch.zeros(mesh.n_tri, dtype=torch.float64, device="cuda"))
+        meta.append((mesh, kap, u0))
+    batch = B.irk_batch_create(ctxs, nsteps, every, u0s, uNs, cks, lams, grads)
+    stats, _ = B.irk_batch_run(batch)
+    assert all(st["steps"] == nsteps and st["resid"] <= 1e-10 for st in stats)
+    for q, ctx in enumerate(ctxs):
+        uN = torch.empty_like(uNs[q])
+        ck = torch.empty_like(cks[q])
+        B.irk_run(ctx, u0s[q], nsteps, uN, ckpt=ck, ckpt_every=every)
+        assert torch.equal(uN, uNs[q]) and torch.equal(ck, cks[q]), q
+    mesh, kap, u0 = meta[-1]
+    prob = ofem.heat_problem(mesh, kappa=kap)
+    OA, Ob, _ = obt.radau_iia(s)
+    refs, _ = oirk.IRKSolver(prob, OA, Ob, h, kind=None).run(u0, nsteps, direct=True)
+    got = uNs[-1].cpu().numpy()
+    assert np.linalg.norm(got - refs[-1]) <= 1e-8 * np.linalg.norm(refs[-1])
+    batch.close()
+    for ctx in ctxs:
+        ctx.close()
+
+
+if __name__ == "__main__":
+    N = int(sys.argv[1]) if len(sys.argv) > 1 else 256
+    nsteps = int(sys.argv[2]) if len(sys.argv) > 2 else 3
+    precs = tuple(sys.argv[3].split(",")) if len(sys.argv) > 3 else ("f64", "f32", "bf16")
+    print(json.dumps(step_errors(_build(), N, nsteps, precs)))
