@@ -108,8 +108,9 @@ struct CsrD {               // device CSR, FP64 values, int32 indices
   double* val = nullptr;
 };
 
-struct Sell {               // SELL-32
+struct Sell {               // SELL: slices of 32 / tpr rows, tpr threads per row (1: SELL-32)
   int n = 0, ncols = 0, nslices = 0;
+  int tpr = 1;
   int64_t nnz_pad = 0;
   int64_t* sptr = nullptr;  // nslices + 1, element offsets
   int* col = nullptr;       // nnz_pad (padding: column 0, value 0)
@@ -147,20 +148,28 @@ inline SellView<V> view(const Sell& s) {
   return SellView<V>{s.n, s.sptr, s.col, sell_vals<V>(s), s.dcol};
 }
 
-// One operator of a V-cycle level in the V-cycle precision.  Short rows
-// (mean <= 16 entries): SELL-32, one thread per row.  Longer rows: CSR with
-// `lanes` threads per row (4..32) and a shuffle reduction, so a coarse
-// Galerkin row of a few hundred entries is not walked by a single thread.
+// One operator of a V-cycle level in the V-cycle precision, in one of three
+// layouts chosen per operator (row-length rule or the layout autotuner):
+//   lanes ==  1  SELL-32, one thread per row;
+//   lanes == -T  SELL with slices of 32/T rows and T threads per row (T = 2, 4, 8),
+//                each warp load one contiguous run of 32 entries;
+//   lanes ==  L  CSR with L consecutive threads per row (2..32) and a shuffle
+//                reduction, so a coarse Galerkin row of a few hundred entries is
+//                not walked by a single thread.
 struct MatT {
   int n = 0, ncols = 0;
   int64_t nnz = 0;
   int lanes = 1;
-  Sell sell;                 // lanes == 1
+  Sell sell;                 // lanes <= 1
   int* rowptr = nullptr;     // lanes > 1
   int* col = nullptr;
   short* dcol = nullptr;     // lanes > 1, square: 16-bit column offsets from the row, or null
   void* val = nullptr;       // CSR values (V-cycle precision, or BF16)
-  int64_t stored() const { return lanes == 1 ? sell.nnz_pad : nnz; }
+  bool uses_sell() const { return lanes <= 1; }
+  int64_t stored() const { return uses_sell() ? sell.nnz_pad : nnz; }
+  const short* offsets() const { return uses_sell() ? sell.dcol : dcol; }
+  // threads of one launch over the operator
+  int64_t threads() const { return lanes < 0 ? int64_t(sell.nslices) * SELL_C : int64_t(n) * lanes; }
 };
 
 template <typename V>
@@ -175,7 +184,7 @@ struct LMat {
 
 template <typename V>
 inline LMat<V> lmat(const MatT& m) {
-  if (m.lanes == 1) return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell), m.sell.dcol};
+  if (m.uses_sell()) return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell), m.sell.dcol};
   return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), m.dcol};
 }
 
@@ -382,7 +391,7 @@ void scan_exclusive64(const int64_t* in, int64_t* out, int n, cudaStream_t st);
 void csr_upload(const irk_csr& h, CsrD& d, DevPool& pool, cudaStream_t st);
 void csr_alloc(CsrD& d, int n, int ncols, int64_t nnz, DevPool& pool);
 void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, DevPool& pool,
-                 cudaStream_t st);
+                 cudaStream_t st, int tpr = 1);
 void sell_share_pattern(const Sell& pat, const double* csr_vals, const CsrD& A, Sell& S, int want64,
                         int want32, DevPool& pool, cudaStream_t st);
 // single-float pair copies of M, F and h A for the operator on FP32 vectors

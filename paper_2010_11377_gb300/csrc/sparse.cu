@@ -219,29 +219,44 @@ void csr_axpby_same_pattern(const CsrD& X, const double* valX, const double* val
 }
 
 // ---------------------------------------------------------------------------
-// CSR -> SELL-32
+// CSR -> SELL: slices of H = 32 / T rows, T threads per row (T = 1: SELL-32).
+// Chunk k of a slice holds 32 entries; entry (row i of the slice, position p of
+// the row) sits at base + (p / T) * 32 + (p % T) * H + i, so every warp load of
+// a chunk is one contiguous run of 32 entries.  Padding: column 0 (offset 0),
+// value 0.
 // ---------------------------------------------------------------------------
-__global__ void k_slice_width(int n, int nslices, const int* __restrict__ rowptr, int64_t* __restrict__ w) {
+__global__ void k_slice_width(int n, int nslices, int tpr, const int* __restrict__ rowptr, int64_t* __restrict__ w) {
   int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslices) return;
+  const int H = SELL_C / tpr;
   int mx = 0;
-  for (int l = 0; l < SELL_C; ++l) {
-    int r = sl * SELL_C + l;
+  for (int l = 0; l < H; ++l) {
+    int r = sl * H + l;
     if (r < n) mx = max(mx, rowptr[r + 1] - rowptr[r]);
   }
-  w[sl] = int64_t(mx) * SELL_C;
+  w[sl] = int64_t((mx + tpr - 1) / tpr) * SELL_C;
 }
 
-__global__ void k_sell_fill(int n, int nslices, const int* __restrict__ rowptr, const int* __restrict__ col,
+// one thread per (slice, lane): lane = q * H + i serves positions q, q + T, ...
+// of row i of the slice
+__device__ __forceinline__ void sell_slot(int t, int tpr, int& sl, int& lane, int& r, int& q) {
+  const int H = SELL_C / tpr;
+  sl = t / SELL_C;
+  lane = t % SELL_C;
+  r = sl * H + lane % H;
+  q = lane / H;
+}
+
+__global__ void k_sell_fill(int n, int nslices, int tpr, const int* __restrict__ rowptr, const int* __restrict__ col,
                             const double* __restrict__ val, const int64_t* __restrict__ sptr,
                             int* __restrict__ scol, double* __restrict__ v64, float* __restrict__ v32,
                             __nv_bfloat16* __restrict__ v16) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nslices * SELL_C) return;
-  int sl = t / SELL_C, lane = t % SELL_C;
+  int sl, lane, r, q;
+  sell_slot(t, tpr, sl, lane, r, q);
   int64_t base = sptr[sl];
   int w = static_cast<int>((sptr[sl + 1] - base) / SELL_C);
-  int r = t;
   int beg = 0, len = 0;
   if (r < n) {
     beg = rowptr[r];
@@ -249,11 +264,12 @@ __global__ void k_sell_fill(int n, int nslices, const int* __restrict__ rowptr, 
   }
   for (int k = 0; k < w; ++k) {
     int64_t idx = base + int64_t(k) * SELL_C + lane;
+    int p = k * tpr + q;
     int c = 0;
     double v = 0.0;
-    if (k < len) {
-      c = col[beg + k];
-      v = val[beg + k];
+    if (p < len) {
+      c = col[beg + p];
+      v = val[beg + p];
     }
     scol[idx] = c;
     if (v64) v64[idx] = v;
@@ -284,18 +300,20 @@ __global__ void k_sell_fill_vals(int n, int nslices, const int* __restrict__ row
 }
 
 // 16-bit column offsets from the row; flag set if one does not fit
-__global__ void k_sell_offsets(int n, int nslices, const int* __restrict__ rowptr, const int64_t* __restrict__ sptr,
-                               const int* __restrict__ scol, short* __restrict__ dcol, int* __restrict__ overflow) {
+__global__ void k_sell_offsets(int n, int nslices, int tpr, const int* __restrict__ rowptr,
+                               const int64_t* __restrict__ sptr, const int* __restrict__ scol,
+                               short* __restrict__ dcol, int* __restrict__ overflow) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nslices * SELL_C) return;
-  int sl = t / SELL_C, lane = t % SELL_C;
+  int sl, lane, r, q;
+  sell_slot(t, tpr, sl, lane, r, q);
   int64_t base = sptr[sl];
   int w = static_cast<int>((sptr[sl + 1] - base) / SELL_C);
-  int len = t < n ? rowptr[t + 1] - rowptr[t] : 0;
+  int len = r < n ? rowptr[r + 1] - rowptr[r] : 0;
   bool bad = false;
   for (int k = 0; k < w; ++k) {
     int64_t idx = base + int64_t(k) * SELL_C + lane;
-    int d = k < len ? scol[idx] - t : 0;
+    int d = (k * tpr + q) < len ? scol[idx] - r : 0;
     if (d < -32767 || d > 32767) {
       bad = true;
       d = 0;
@@ -323,17 +341,20 @@ __global__ void k_csr_offsets(int n, const int* __restrict__ rowptr, const int* 
 }
 
 void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, DevPool& pool,
-                 cudaStream_t st) {
+                 cudaStream_t st, int tpr) {
+  if (tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8) fail(IRK_ERR_INVALID, "SELL threads per row must be 1, 2, 4 or 8");
+  const int H = SELL_C / tpr;
   S.n = A.n;
   S.ncols = A.ncols;
-  S.nslices = (A.n + SELL_C - 1) / SELL_C;
+  S.tpr = tpr;
+  S.nslices = (A.n + H - 1) / H;
   int ns = S.nslices;
   S.sptr = pool.get<int64_t>(ns + 1);
   {
     Tmp tmp;
     int64_t* w = tmp.get<int64_t>(ns > 0 ? ns : 1);
     if (ns > 0) {
-      k_slice_width<<<(ns + 255) / 256, 256, 0, st>>>(A.n, ns, A.rowptr, w);
+      k_slice_width<<<(ns + 255) / 256, 256, 0, st>>>(A.n, ns, tpr, A.rowptr, w);
       CK_LAUNCH();
     }
     scan_exclusive64(w, S.sptr, ns, st);
@@ -346,7 +367,7 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
   S.v16 = want16 ? pool.get<__nv_bfloat16>(np) : nullptr;
   if (ns > 0) {
     int nt = ns * SELL_C;
-    k_sell_fill<<<(nt + 255) / 256, 256, 0, st>>>(A.n, ns, A.rowptr, A.col, A.val, S.sptr, S.col, S.v64,
+    k_sell_fill<<<(nt + 255) / 256, 256, 0, st>>>(A.n, ns, tpr, A.rowptr, A.col, A.val, S.sptr, S.col, S.v64,
                                                   S.v32, S.v16);
     CK_LAUNCH();
   }
@@ -357,7 +378,7 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
     int* ovf = tmp.get<int>(1);
     CK(cudaMemsetAsync(ovf, 0, sizeof(int), st));
     int nt = ns * SELL_C;
-    k_sell_offsets<<<(nt + 255) / 256, 256, 0, st>>>(A.n, ns, A.rowptr, S.sptr, S.col, dc, ovf);
+    k_sell_offsets<<<(nt + 255) / 256, 256, 0, st>>>(A.n, ns, tpr, A.rowptr, S.sptr, S.col, dc, ovf);
     CK_LAUNCH();
     if (read_scalar(ovf, st) == 0) S.dcol = dc;
   }
@@ -367,6 +388,7 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
 // A second value array on an existing SELL pattern (M and F share one pattern)
 void sell_share_pattern(const Sell& pat, const double* csr_vals, const CsrD& A, Sell& S, int want64,
                         int want32, DevPool& pool, cudaStream_t st) {
+  if (pat.tpr != 1) fail(IRK_ERR_INVALID, "shared SELL patterns have one thread per row");
   S = pat;
   S.v64 = nullptr;
   S.v32 = nullptr;
@@ -408,8 +430,8 @@ int choose_lanes(int64_t nnz, int n) {
 // ---------------------------------------------------------------------------
 // Layout autotuner: for an operator of a given shape class (log2 of the rows,
 // log2 of the mean row length, precision) time y = A x with every candidate
-// thread tile (SELL thread-per-row, or CSR with 2..32 lanes per row) and keep
-// the fastest.  Decisions are cached for the process, so repeated set-ups
+// thread tile (SELL thread-per-row, sliced SELL with 2, 4 or 8 threads per row,
+// or CSR with 2..32 lanes per row) and keep the fastest.  Decisions are cached for the process, so repeated set-ups
 // (batches, kappa updates) reuse them.  IRK_AUTOTUNE=0 uses the row-length rule.
 // ---------------------------------------------------------------------------
 namespace {
@@ -433,7 +455,20 @@ bool autotune_enabled() {
 
 static void build_layout(const CsrD& A, MatT& m, int prec, int lanes, DevPool& pool, cudaStream_t st);
 
+// IRK_LAYOUT=<code> (1, -2, -4, -8, 2, 4, 8, 16, 32) puts every V-cycle operator
+// in that layout (diagnosis and layout tests; every layout is exact for any row
+// length, only its speed differs)
+static int forced_layout() {
+  const char* e = std::getenv("IRK_LAYOUT");
+  if (!e) return 0;
+  int v = std::atoi(e);
+  for (int c : {1, -2, -4, -8, 2, 4, 8, 16, 32})
+    if (v == c) return v;
+  return 0;
+}
+
 int autotune_lanes(const CsrD& A, int prec, cudaStream_t st) {
+  if (int f = forced_layout()) return f;
   int heuristic = choose_lanes(A.nnz, A.n);
   if (!autotune_enabled() || A.n < 64 || A.nnz == 0) return heuristic;
   double avg = double(A.nnz) / A.n;
@@ -443,7 +478,8 @@ int autotune_lanes(const CsrD& A, int prec, cudaStream_t st) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;
   }
-  const int cand[] = {1, 2, 4, 8, 16, 32};
+  // SELL-32, sliced SELL with 2/4/8 threads per row, CSR with 2..32 lanes
+  const int cand[] = {1, -2, -4, -8, 2, 4, 8, 16, 32};
   size_t es = prec == 64 ? 8 : 4;
   DevPool tmp;
   void* x = tmp.alloc(es * (A.ncols > 0 ? A.ncols : 1));
@@ -461,6 +497,7 @@ int autotune_lanes(const CsrD& A, int prec, cudaStream_t st) {
   for (int L : cand) {
     if (L != heuristic && L > 1 && avg < L / 2.0) continue;   // more lanes than half the row: idle lanes
     if (L != heuristic && L == 1 && avg > 48.0) continue;      // one thread walking a long row
+    if (L < 0 && (avg < 2.0 * -L || avg > 96.0)) continue;     // sliced: at least 2 entries per thread, medium rows
     MatT m;
     DevPool mp;
     build_layout(A, m, prec, L, mp, st);
@@ -483,6 +520,9 @@ int autotune_lanes(const CsrD& A, int prec, cudaStream_t st) {
     mp.free_all();
   }
   if (best != heuristic && !(best_t < 0.9f * t_rule)) best = heuristic;
+  if (const char* v = std::getenv("IRK_VERBOSE"); v && std::atoi(v) > 0)
+    std::fprintf(stderr, "irk autotune: %d rows, %.1f entries per row, prec %d: layout %d (rule %d: %.4f ms, best %.4f ms per 10)\n",
+                 A.n, avg, prec, best, heuristic, double(t_rule), double(best_t));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   tmp.free_all();
@@ -502,8 +542,8 @@ static void build_layout(const CsrD& A, MatT& m, int prec, int lanes, DevPool& p
   m.ncols = A.ncols;
   m.nnz = A.nnz;
   m.lanes = lanes;
-  if (m.lanes == 1) {
-    csr_to_sell(A, m.sell, prec == 64, prec == 32, prec == 16, pool, st);
+  if (m.uses_sell()) {
+    csr_to_sell(A, m.sell, prec == 64, prec == 32, prec == 16, pool, st, lanes < 0 ? -lanes : 1);
     return;
   }
   m.rowptr = A.rowptr;

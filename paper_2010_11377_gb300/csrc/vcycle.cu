@@ -45,14 +45,31 @@ SmoothCoef smooth_coefficients(const AmgParams& p) {
 // x^(0) implicit: x1 = beta0 * dinv * b
 enum { XM_EXPLICIT = 0, XM_IMPLICIT = 1, XM_ZERO = 2 };
 
-// Row product sum_c a_rc x(c) of operator A at row r (r < 0: an idle group
+// Thread -> (row, lane) of an operator layout (see MatT): L >= 1 gives L
+// consecutive threads per row; L = -T gives the sliced SELL mapping, where the
+// 32 threads of a warp serve the 32/T rows of one slice, T threads per row.
+template <int L>
+__device__ __forceinline__ void row_lane(int gid, int& r, int& lane) {
+  if constexpr (L < 0) {
+    constexpr int H = 32 / (-L);
+    const int t = gid & 31;
+    r = (gid >> 5) * H + (t % H);
+    lane = t / H;
+  } else {
+    r = gid / L;
+    lane = gid % L;
+  }
+}
+
+// Row product sum_c a_rc x(c) of operator A at row r (r < 0: an idle thread
 // that only takes part in the shuffles).  L == 1: SELL-32, one thread per row;
-// L > 1: CSR, L consecutive lanes per row, strided over the row, reduced by an
-// xor-shuffle so every lane of the group holds the sum.
+// L == -T: sliced SELL, T threads per row reduced by xor-shuffles across the
+// slice; L > 1: CSR, L consecutive lanes per row, strided over the row, reduced
+// by an xor-shuffle.  Every thread of a row's group ends with the sum.
 template <int L, typename V, typename T, typename XF>
 __device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
   T acc = T(0);
-  if (L == 1) {
+  if constexpr (L == 1) {
     if (r >= 0) {
       int sl = r >> 5, ln = r & 31;
       int64_t base = A.sptr[sl];
@@ -69,6 +86,27 @@ __device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
         }
       }
     }
+  } else if constexpr (L < 0) {
+    constexpr int H = 32 / (-L);
+    if (r >= 0) {
+      const int sl = r / H, i = r - sl * H;
+      const int64_t base = A.sptr[sl];
+      const int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
+      const int64_t off = base + lane * H + i;
+      if (A.dcol) {
+        for (int k = 0; k < w; ++k) {
+          int64_t idx = off + (int64_t(k) << 5);
+          acc = fma(widen(A.val[idx]), xf(r + static_cast<int>(A.dcol[idx])), acc);
+        }
+      } else {
+        for (int k = 0; k < w; ++k) {
+          int64_t idx = off + (int64_t(k) << 5);
+          acc = fma(widen(A.val[idx]), xf(A.col[idx]), acc);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= H; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   } else {
     if (r >= 0) {
       int e = A.rowptr[r + 1];
@@ -94,7 +132,8 @@ k_smooth(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T
   pdl_trigger();
   pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = gid / L, lane = gid % L;
+  int r, lane;
+  row_lane<L>(gid, r, lane);
   bool valid = r < A.n;
   T ax = T(0);
   if (XM != XM_ZERO)
@@ -130,7 +169,8 @@ k_resid(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T*
   pdl_trigger();
   pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = gid / L, lane = gid % L;
+  int r, lane;
+  row_lane<L>(gid, r, lane);
   bool valid = r < A.n;
   T ax = row_dot<L, V, T>(A, valid ? r : -1, lane, [&](int c) {
     return (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : x[c];
@@ -145,7 +185,8 @@ k_spmv(LMat<T> A, const T* __restrict__ x, T* __restrict__ y) {
   pdl_trigger();
   pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = gid / L, lane = gid % L;
+  int r, lane;
+  row_lane<L>(gid, r, lane);
   bool valid = r < A.n;
   T s = row_dot<L, T, T>(A, valid ? r : -1, lane, [&](int c) { return x[c]; });
   if (valid && lane == 0) y[r] = s;
@@ -158,7 +199,8 @@ k_prolong(LMat<T> P, const T* __restrict__ e, T* x, const T* __restrict__ dinv, 
   pdl_trigger();
   pdl_wait();
   int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = gid / L, lane = gid % L;
+  int r, lane;
+  row_lane<L>(gid, r, lane);
   bool valid = r < P.n;
   T s = row_dot<L, T, T>(P, valid ? r : -1, lane, [&](int c) { return e[c]; });
   if (valid && lane == 0) x[r] = (IMPLICIT ? beta0 * dinv[r] * b[r] : x[r]) + s;
@@ -194,6 +236,9 @@ __global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
 // dispatch on the lanes-per-row of an operator
 #define IRK_DISPATCH_L(LANES, ...)                          \
   switch (LANES) {                                          \
+    case -8: { constexpr int LN = -8; __VA_ARGS__; } break;  \
+    case -4: { constexpr int LN = -4; __VA_ARGS__; } break;  \
+    case -2: { constexpr int LN = -2; __VA_ARGS__; } break;  \
     case 1: { constexpr int LN = 1; __VA_ARGS__; } break;    \
     case 2: { constexpr int LN = 2; __VA_ARGS__; } break;    \
     case 4: { constexpr int LN = 4; __VA_ARGS__; } break;    \
@@ -203,7 +248,7 @@ __global__ void k_copy_out(int n, const T* __restrict__ src, JPtr<T> out) {
     default: fail(IRK_ERR_INVALID, "bad lanes per row");    \
   }
 
-static inline unsigned grid_for(const MatT& m) { return nblk(int64_t(m.n) * m.lanes); }
+static inline unsigned grid_for(const MatT& m) { return nblk(m.threads()); }
 
 // y = m x in the V-cycle precision (prec 64: FP64, else FP32 vectors); used by
 // the layout autotuner
@@ -239,7 +284,7 @@ struct VCycle {
 
   template <typename V>
   void count_matvec(const Level& L, int vec_reads, int vec_writes) {
-    const double idx_bytes = (L.Am.lanes == 1 ? L.Am.sell.dcol : L.Am.dcol) ? 2.0 : 4.0;   // 16-bit offsets
+    const double idx_bytes = L.Am.offsets() ? 2.0 : 4.0;   // 16-bit offsets
     cost.bytes += double(L.nnz) * (idx_bytes + sizeof(V)) + double(L.n) * sizeof(T) * (vec_reads + vec_writes);
     cost.flops += 2.0 * double(L.nnz) + 4.0 * L.n;
   }
