@@ -887,7 +887,7 @@ irk_status irk_profile(irk_ctx* h, int32_t which, int32_t j, int32_t warm, int32
       case IRK_PROF_KRON: {
         launch = [&] { irk::profile_kron_launch(c, c.stream); };
         double zs = c.amg.amg_prec == 64 ? 8.0 : 4.0;
-        const double idx = c.Ms.dcol ? 2.0 : 4.0;
+        const double idx = irk::offset_bytes_per_entry(c.Ms);
         // per nonzero: M and F (two FP64, or one float4 of single-float pairs) and its column
         B = double(c.Mc.nnz) * (16.0 + idx) + double(c.N) * (zs + 8.0);
         Fl = 2.0 * (2.0 * c.s * double(c.Mc.nnz) + double(c.s) * c.s * c.n);

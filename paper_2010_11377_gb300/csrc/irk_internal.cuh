@@ -118,6 +118,14 @@ struct Sell {               // SELL: slices of 32 / tpr rows, tpr threads per ro
   // same columns as 16-bit offsets from the row (padding: offset 0), read by
   // the bandwidth-bound kernels instead of col (2 bytes per entry less)
   short* dcol = nullptr;
+  // SELL-32 with 16-bit offsets: slices whose 32 rows all have the same length
+  // and the same offsets (the interior of a stencil in natural order) keep one
+  // offset per chunk, pdcol[sptr[sl] / 32 + k], read once per warp instead of
+  // 32 times; suni[sl] = 1 marks them.  nnz_nonuni counts the stored entries of
+  // the other slices (whose per-entry offsets are read).
+  unsigned char* suni = nullptr;
+  short* pdcol = nullptr;
+  int64_t nnz_nonuni = 0;
   double* v64 = nullptr;
   float* v32 = nullptr;
   __nv_bfloat16* v16 = nullptr;
@@ -130,6 +138,8 @@ struct SellView {
   const int* __restrict__ col;
   const V* __restrict__ val;
   const short* __restrict__ dcol;
+  const unsigned char* __restrict__ suni;   // uniform-pattern slices, or null
+  const short* __restrict__ pdcol;          // their per-chunk offsets
 };
 
 // column of SELL entry idx of row r
@@ -145,7 +155,7 @@ template <> inline const __nv_bfloat16* sell_vals<__nv_bfloat16>(const Sell& s) 
 
 template <typename V>
 inline SellView<V> view(const Sell& s) {
-  return SellView<V>{s.n, s.sptr, s.col, sell_vals<V>(s), s.dcol};
+  return SellView<V>{s.n, s.sptr, s.col, sell_vals<V>(s), s.dcol, s.suni, s.pdcol};
 }
 
 // One operator of a V-cycle level in the V-cycle precision, in one of three
@@ -180,12 +190,23 @@ struct LMat {
   const int* __restrict__ col;
   const V* __restrict__ val;
   const short* __restrict__ dcol;   // 16-bit column offsets from the row (SELL or CSR), or null
+  const unsigned char* __restrict__ suni;   // SELL-32: uniform-pattern slices, or null
+  const short* __restrict__ pdcol;
 };
 
 template <typename V>
 inline LMat<V> lmat(const MatT& m) {
-  if (m.uses_sell()) return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell), m.sell.dcol};
-  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), m.dcol};
+  if (m.uses_sell())
+    return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell), m.sell.dcol, m.sell.suni,
+                   m.sell.pdcol};
+  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), m.dcol, nullptr, nullptr};
+}
+
+// bytes of column information per stored entry that a product reads
+inline double offset_bytes_per_entry(const Sell& s) {
+  if (!s.dcol) return 4.0;
+  if (!s.suni || s.nnz_pad == 0) return 2.0;
+  return 2.0 * double(s.nnz_nonuni) / double(s.nnz_pad);
 }
 
 // ---------------------------------------------------------------------------

@@ -64,6 +64,17 @@ bool pdl_enabled() {
   return on == 1;
 }
 
+// shared per-slice offset patterns in SELL-32 (IRK_SLICE_PATTERN=0 reads the
+// per-entry offsets everywhere)
+static bool slice_patterns_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("IRK_SLICE_PATTERN");
+    on = (e && std::atoi(e) == 0) ? 0 : 1;
+  }
+  return on == 1;
+}
+
 // 16-bit column offsets in the SELL and CSR layouts of square operators
 // (IRK_SELL16=0 keeps 32-bit columns everywhere)
 static bool sell_offsets_enabled() {
@@ -323,6 +334,32 @@ __global__ void k_sell_offsets(int n, int nslices, int tpr, const int* __restric
   if (bad) atomicOr(overflow, 1);
 }
 
+// one warp per SELL-32 slice: the slice shares one offset pattern when its 32
+// rows are all real, all as long as the slice is wide, and agree chunk by chunk
+__global__ void k_sell_uniform(int n, int nslices, const int* __restrict__ rowptr, const int64_t* __restrict__ sptr,
+                               const short* __restrict__ dcol, unsigned char* __restrict__ suni,
+                               short* __restrict__ pdcol, unsigned long long* __restrict__ nonuni) {
+  int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (sl >= nslices) return;
+  int64_t base = sptr[sl];
+  int w = static_cast<int>((sptr[sl + 1] - base) >> 5);
+  int r = sl * SELL_C + lane;
+  bool ok = r < n && (rowptr[r + 1] - rowptr[r]) == w;
+  for (int k = 0; k < w; ++k) {
+    short d = dcol[base + (int64_t(k) << 5) + lane];
+    short d0 = __shfl_sync(0xffffffffu, d, 0);
+    ok = ok && d == d0;
+  }
+  bool all = __all_sync(0xffffffffu, ok);
+  if (lane == 0) {
+    suni[sl] = all ? 1 : 0;
+    if (!all) atomicAdd(nonuni, static_cast<unsigned long long>(w) * SELL_C);
+  }
+  if (all)
+    for (int k = lane; k < w; k += 32) pdcol[(base >> 5) + k] = dcol[base + (int64_t(k) << 5)];
+}
+
 // the same for CSR (one thread per row)
 __global__ void k_csr_offsets(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
                               short* __restrict__ dcol, int* __restrict__ overflow) {
@@ -381,6 +418,20 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
     k_sell_offsets<<<(nt + 255) / 256, 256, 0, st>>>(A.n, ns, tpr, A.rowptr, S.sptr, S.col, dc, ovf);
     CK_LAUNCH();
     if (read_scalar(ovf, st) == 0) S.dcol = dc;
+  }
+  S.suni = nullptr;
+  S.pdcol = nullptr;
+  S.nnz_nonuni = S.nnz_pad;
+  if (S.dcol && tpr == 1 && sell_offsets_enabled() && slice_patterns_enabled()) {
+    S.suni = pool.get<unsigned char>(ns);
+    S.pdcol = pool.get<short>(np / SELL_C + 1);
+    Tmp tmp;
+    unsigned long long* nonuni = tmp.get<unsigned long long>(1);
+    CK(cudaMemsetAsync(nonuni, 0, sizeof(unsigned long long), st));
+    k_sell_uniform<<<(ns * SELL_C + 255) / 256, 256, 0, st>>>(A.n, ns, A.rowptr, S.sptr, S.dcol, S.suni, S.pdcol,
+                                                              nonuni);
+    CK_LAUNCH();
+    S.nnz_nonuni = static_cast<int64_t>(read_scalar(nonuni, st));
   }
   CK(cudaStreamSynchronize(st));
 }

@@ -74,7 +74,14 @@ __device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
       int sl = r >> 5, ln = r & 31;
       int64_t base = A.sptr[sl];
       int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-      if (A.dcol) {
+      if (A.suni && A.suni[sl]) {
+        // the slice's shared pattern: one offset per chunk for the whole warp
+        const short* __restrict__ pd = A.pdcol + (base >> 5);
+        for (int k = 0; k < w; ++k) {
+          int64_t idx = base + (int64_t(k) << 5) + ln;
+          acc = fma(widen(A.val[idx]), xf(r + static_cast<int>(pd[k])), acc);
+        }
+      } else if (A.dcol) {
         for (int k = 0; k < w; ++k) {
           int64_t idx = base + (int64_t(k) << 5) + ln;
           acc = fma(widen(A.val[idx]), xf(r + static_cast<int>(A.dcol[idx])), acc);
@@ -284,7 +291,8 @@ struct VCycle {
 
   template <typename V>
   void count_matvec(const Level& L, int vec_reads, int vec_writes) {
-    const double idx_bytes = L.Am.offsets() ? 2.0 : 4.0;   // 16-bit offsets
+    const double idx_bytes = L.Am.uses_sell() ? offset_bytes_per_entry(L.Am.sell)
+                                               : (L.Am.dcol ? 2.0 : 4.0);   // 16-bit / shared offsets
     cost.bytes += double(L.nnz) * (idx_bytes + sizeof(V)) + double(L.n) * sizeof(T) * (vec_reads + vec_writes);
     cost.flops += 2.0 * double(L.nnz) + 4.0 * L.n;
   }
@@ -528,9 +536,10 @@ k_sweep_rhs(SellView<T> F, const double* __restrict__ V, const int* __restrict__
   int sl = r >> 5, lane = r & 31;
   int64_t base = F.sptr[sl];
   int w = static_cast<int>((F.sptr[sl + 1] - base) >> 5);
+  const short* __restrict__ pd = (F.suni && F.suni[sl]) ? F.pdcol + (base >> 5) : nullptr;
   for (int k = 0; k < w; ++k) {
     int64_t idx = base + (int64_t(k) << 5) + lane;
-    int c = sell_col(F.col, F.dcol, idx, r);
+    int c = pd ? r + static_cast<int>(pd[k]) : sell_col(F.col, F.dcol, idx, r);
     T f = F.val[idx];
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc[q] = fma(f, zj[int64_t(cp.idx[q]) * n + c], acc[q]);
@@ -587,7 +596,7 @@ int precond_launch(Ctx& c, const PrecondArgs& a, bool transpose, cudaStream_t st
     if (a.bytes) {
       const Sell& F = c.Fs;
       double sv = f64 ? 8.0 : 4.0;
-      *a.bytes += double(c.Fc.nnz) * (4.0 + sv) * (cp.n > 0 ? 1 : 0) + double(n) * (8.0 + sv) +
+      *a.bytes += double(c.Fc.nnz) * (offset_bytes_per_entry(F) + sv) * (cp.n > 0 ? 1 : 0) + double(n) * (8.0 + sv) +
                   double(n) * sv * cp.n;
       *a.flops += 2.0 * double(c.Fc.nnz) * cp.n + 2.0 * n * cp.n;
       (void)F;

@@ -74,9 +74,11 @@ def gpu():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("layout", [1, -2, -4, -8, 4])
-def test_layout_against_oracle(gpu, layout):
-    env = dict(os.environ, IRK_LAYOUT=str(layout))
+@pytest.mark.parametrize("layout,pattern", [(1, "1"), (1, "0"), (-2, "1"), (-4, "1"), (-8, "1"), (4, "1")])
+def test_layout_against_oracle(gpu, layout, pattern):
+    """pattern "0": SELL-32 reads every entry's own column offset instead of the
+    shared per-slice pattern (IRK_SLICE_PATTERN=0)."""
+    env = dict(os.environ, IRK_LAYOUT=str(layout), IRK_SLICE_PATTERN=pattern)
     r = subprocess.run([sys.executable, os.path.abspath(__file__)], env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
