@@ -192,17 +192,14 @@ struct LMat {
   const short* __restrict__ dcol;   // 16-bit column offsets from the row (SELL or CSR), or null
   const unsigned char* __restrict__ suni;   // SELL-32: uniform-pattern slices, or null
   const short* __restrict__ pdcol;
-  int unroll;                               // SELL-32 rows of <= 8 entries: all loads first
 };
-
-bool row_unroll_enabled();
 
 template <typename V>
 inline LMat<V> lmat(const MatT& m) {
   if (m.uses_sell())
     return LMat<V>{m.n, m.sell.sptr, nullptr, m.sell.col, sell_vals<V>(m.sell), m.sell.dcol, m.sell.suni,
-                   m.sell.pdcol, row_unroll_enabled() ? 1 : 0};
-  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), m.dcol, nullptr, nullptr, 0};
+                   m.sell.pdcol};
+  return LMat<V>{m.n, nullptr, m.rowptr, m.col, static_cast<const V*>(m.val), m.dcol, nullptr, nullptr};
 }
 
 // bytes of column information per stored entry that a product reads

@@ -11,22 +11,11 @@
 #include "irk_internal.cuh"
 
 #include <cmath>
-#include <cstdlib>
 
 namespace irk {
 
 template <typename T> __device__ __forceinline__ T widen(T v) { return v; }
 __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// IRK_ROW_UNROLL=0: short SELL-32 rows walked entry by entry (A/B switch)
-bool row_unroll_enabled() {
-  static int on = -1;
-  if (on < 0) {
-    const char* e = std::getenv("IRK_ROW_UNROLL");
-    on = (e && std::atoi(e) == 0) ? 0 : 1;
-  }
-  return on == 1;
-}
 
 SmoothCoef smooth_coefficients(const AmgParams& p) {
   SmoothCoef c;
@@ -85,28 +74,7 @@ __device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
       int sl = r >> 5, ln = r & 31;
       int64_t base = A.sptr[sl];
       int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-      if (A.unroll && w <= 8 && A.dcol) {
-        // short rows: issue every column, value and gather of the row before the
-        // first FMA (one memory latency per row instead of one per entry); the
-        // sum runs in the same order as the loop below
-        const short* __restrict__ pd = (A.suni && A.suni[sl]) ? A.pdcol + (base >> 5) : nullptr;
-        int off[8];
-        V av[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < w) {
-            const int64_t idx = base + (int64_t(k) << 5) + ln;
-            off[k] = pd ? static_cast<int>(pd[k]) : static_cast<int>(A.dcol[idx]);
-            av[k] = A.val[idx];
-          }
-        T xv[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < w) xv[k] = xf(r + off[k]);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < w) acc = fma(widen(av[k]), xv[k], acc);
-      } else if (A.suni && A.suni[sl]) {
+      if (A.suni && A.suni[sl]) {
         // the slice's shared pattern: one offset per chunk for the whole warp
         const short* __restrict__ pd = A.pdcol + (base >> 5);
         for (int k = 0; k < w; ++k) {
