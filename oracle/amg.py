@@ -26,6 +26,12 @@ reading fixed in the design notes, step by step:
              power iteration on the similar S = |D|^{-1/2} A |D|^{-1/2} from
              the +-1 vector x_i = +1 iff fmix32(i ^ 0x68E31DA4) is odd:
              x <- S x / ||x||, rho = ||S x_19|| / ||x_19||.
+  SUPG       with a streamline-diffusion matrix T and the block coefficient c
+             (block M + c F of a SUPG problem), every coarse level adds the
+             streamline diffusion of its larger mesh size:
+             A_c = P^T A P + c (f_c - f) T_c, T_c = P^T T P, f = sqrt(n_0 / n)
+             (the coarse-level stabilisation of Section 5); the stabilised A_c
+             is the one that is coarsened further.
   coarse     A_c = P^T A P (Galerkin, R = P^T), until n <= coarse_max (2048) or
              coarsening stalls (the next level would keep more than 90% of the
              rows); the coarsest level is solved directly (dense LU) when it
@@ -207,7 +213,7 @@ class Hierarchy:
 
     def __init__(self, A, theta=0.08, coarse_max=2048, max_levels=12,
                  nu_pre=1, nu_post=1, smoother="chebyshev", cheb_degree=4,
-                 cheb_lo=0.1, p_smooth=2, strength_negative=False):
+                 cheb_lo=0.1, p_smooth=2, strength_negative=False, stab=None):
         self.theta = theta
         self.nu_pre = nu_pre
         self.nu_post = nu_post
@@ -217,6 +223,9 @@ class Hierarchy:
         self.cheb_degree = cheb_degree
         self.cheb_lo = cheb_lo
         self.levels = [Level(A)]
+        T, c_stab = (None, 0.0) if stab is None else stab
+        n0 = self.levels[0].n
+        f_prev = 1.0
         while True:
             lev = self.levels[-1]
             lvl = len(self.levels) - 1
@@ -238,6 +247,11 @@ class Hierarchy:
             lev.R = P.T.tocsr()
             lev.agg = agg
             Ac = (lev.R @ lev.A @ P).tocsr()
+            if T is not None:
+                T = (lev.R @ T @ P).tocsr()
+                f = float(np.sqrt(n0 / nc))
+                Ac = (Ac + (c_stab * (f - f_prev)) * T).tocsr()
+                f_prev = f
             self.levels.append(Level(Ac))
         last = self.levels[-1]
         self.coarse_max = coarse_max

@@ -230,6 +230,33 @@ def supg_parameter(area, G, w_c, eps):
     return delta
 
 
+def streamline_matrix(mesh, eps, wind):
+    """All-node streamline-diffusion matrix of the coarse-level SUPG
+    stabilisation: T[i,j] = sum over elements with mesh Peclet number P_e > 1
+    of h_e/(2|w_e|) |T| (w_e . grad l_i)(w_e . grad l_j), with h_e, P_e and the
+    centroid wind w_e of supg_parameter (the large-Peclet slope of delta_e in
+    the element size)."""
+    xy, tri = mesh.xy, mesh.tri
+    area, G = element_geometry(xy, tri)
+    p = xy[tri]
+    centroid = p.mean(axis=1)
+    w_c = wind(centroid[:, 0], centroid[:, 1])
+    wn = np.linalg.norm(w_c, axis=1)
+    wcg = np.einsum("ei,eai->ea", w_c, G)
+    proj = np.abs(wcg).sum(axis=1)
+    he = np.where(proj > 0, 2.0 * wn / np.where(proj > 0, proj, 1.0), 0.0)
+    Pe = wn * he / (2.0 * eps)
+    slope = np.where(Pe > 1.0, he / (2.0 * np.where(wn > 0, wn, 1.0)), 0.0)
+    Te = (slope * area)[:, None, None] * wcg[:, :, None] * wcg[:, None, :]
+    rows = np.repeat(tri, 3, axis=1).ravel()
+    cols = np.tile(tri, (1, 3)).ravel()
+    n = xy.shape[0]
+    T = sp.csr_matrix((Te.ravel(), (rows, cols)), shape=(n, n))
+    T.sum_duplicates()
+    T.sort_indices()
+    return T
+
+
 def double_glazing_supg_nitsche(mesh, eps, wind, ub, gamma=10.0):
     """All-node matrices of
         (M + S_M) u' + (eps K + C + S + N) u = G
@@ -295,7 +322,9 @@ def double_glazing_supg_nitsche(mesh, eps, wind, ub, gamma=10.0):
     F.sum_duplicates()
     M.sort_indices()
     F.sort_indices()
-    return Problem(M, F, -load, mesh, eps=eps, kind="double_glazing_supg")
+    prob = Problem(M, F, -load, mesh, eps=eps, kind="double_glazing_supg")
+    prob.T = streamline_matrix(mesh, eps, wind)
+    return prob
 
 
 def supg_load(mesh, eps, wind, f):

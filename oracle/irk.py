@@ -51,13 +51,15 @@ class BlockPreconditioner:
     kind DU (A~ upper): backward substitution,
         (M + h A~_jj F) w_j = v_j - sum_{k>j} h A~_jk F w_k.
     Each subsolve is exact (sparse LU, ``subsolve='direct'``) or one AMG
-    V-cycle on the block (``subsolve='amg'``).
+    V-cycle on the block (``subsolve='amg'``); ``stab`` (a SUPG problem's
+    streamline matrix T) stabilises the coarse AMG levels of the block
+    M + h A~_jj F with c = h A~_jj.
     ``transpose=True`` applies P^T (for symmetric M, F: I (x) M + h A~^T (x) F,
     whose substitution runs in the opposite direction).
     """
 
     def __init__(self, M, F, A, h, kind="LD", subsolve="amg", Atilde=None,
-                 amg_opts=None, transpose=False):
+                 amg_opts=None, transpose=False, stab=None):
         self.kind = kind.upper()
         self.At = np.array(Atilde if Atilde is not None else bt.atilde(A, self.kind))
         direction = bt.sweep_direction(self.kind)
@@ -78,7 +80,8 @@ class BlockPreconditioner:
             if subsolve == "direct":
                 self.solvers.append(spla.splu(Bj.tocsc()))
             elif subsolve == "amg":
-                self.solvers.append(Hierarchy(Bj, **amg_opts))
+                st = None if stab is None else (stab, h * self.At[j, j])
+                self.solvers.append(Hierarchy(Bj, stab=st, **amg_opts))
             else:
                 raise ValueError(subsolve)
 
@@ -287,7 +290,8 @@ class IRKSolver:
         self.pc = None
         if kind is not None:
             self.pc = BlockPreconditioner(self.M, self.F, self.A, self.h, kind,
-                                          subsolve, Atilde=Atilde, amg_opts=amg_opts)
+                                          subsolve, Atilde=Atilde, amg_opts=amg_opts,
+                                          stab=getattr(prob, "T", None))
         self._pcT = None
 
     def op(self, z):
