@@ -218,7 +218,8 @@ def step_roofline(ctx, prof, its_per_step, ms_per_step, hbm, recorded):
 # 152 SMs at ~1987 MHz): 1.196 TFLOP/s; nominal 1.25 TFLOP/s at 2070 MHz.
 FP64_TFLOPS = 1.196
 
-# AMG options of the SUPG + Nitsche double-glazing sweeps (t12, t13): these blocks are
+# AMG options of the SUPG + Nitsche double-glazing sweeps (t12, t13), which also pass
+# the streamline matrix of the coarse-level SUPG stabilisation: these blocks are
 # convection-dominated once h_t is large, D^-1 A has complex eigenvalues, and a
 # polynomial smoother needs more strength there: Chebyshev degree 8 on [0.3, 1]
 # (the default [0.1, 1] interval amplifies the complex eigenvalues near its low end
@@ -654,7 +655,7 @@ def run_sweep(args):
                     for kind in ("GSL", "LD"):
                         o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", **SUPG_AMG)
                         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o,
-                                          g=p["g"])
+                                          g=p["g"], stab=p["valT"])
                         rhs = torch.empty_like(kstar)
                         B.irk_apply_operator(ctx, kstar, rhs)
                         k = torch.empty_like(kstar)
@@ -681,7 +682,7 @@ def run_sweep(args):
                     for kind in ("GSL", "LD"):
                         o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", **SUPG_AMG)
                         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o,
-                                          g=p["g"])
+                                          g=p["g"], stab=p["valT"])
                         rhs = torch.empty_like(kstar)
                         B.irk_apply_operator(ctx, kstar, rhs)
                         k = torch.empty_like(kstar)

@@ -214,6 +214,18 @@ irk_status irk_fem_assemble_supg(int32_t n_nodes, const double* xy, int32_t n_tr
                                  int64_t* nnz, int64_t* rowptr, int32_t* col, double* valM, double* valF,
                                  double* g);
 
+/* Streamline-diffusion matrix of the coarse-level SUPG stabilisation, on the
+ * pattern (rowptr, col: n_nodes rows, from irk_fem_assemble_supg) of the SUPG
+ * matrices: valT[i,j] = sum over the triangles with mesh Peclet number
+ * P_e = |w_e| h_e/(2 eps) > 1 of h_e/(2|w_e|) |T| (w_e . grad l_i)(w_e . grad l_j),
+ * h_e = 2|w_e| / sum_a |w_e . grad l_a|, w_e = wind_c (n_tri*2, centroid wind).
+ * (h_e/(2|w_e|) is the slope of the SUPG parameter in the element size at large
+ * Peclet numbers.)  IRK_ERR_INVALID for a bad mesh, eps <= 0, or a triangle
+ * entry missing from the pattern. */
+irk_status irk_fem_assemble_streamline(int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri,
+                                       double eps, const double* wind_c, const int64_t* rowptr,
+                                       const int32_t* col, double* valT);
+
 /* ------------------------------------------------------------------------- *
  * Solver context.                                                            *
  * ------------------------------------------------------------------------- */
@@ -228,6 +240,13 @@ typedef struct {
   const double* xy;      /* n_nodes*2 */
   const int32_t* tri;    /* n_tri*3, counter-clockwise */
   const int32_t* dof;    /* n_nodes: interior index or -1 */
+  /* Coarse-level SUPG stabilisation (Section 5: the SUPG discretisation is
+   * stabilised on every coarse mesh of the AMG): nnz values, on the pattern of
+   * M, of the streamline-diffusion matrix T (irk_fem_assemble_streamline), or
+   * NULL.  With T, level l (n_l rows) of the hierarchy of the block M + c F is
+   * A_l = P^T A_{l-1} P + c (f_l - f_{l-1}) T_l, T_l = P^T T_{l-1} P, T_0 = T,
+   * f_l = sqrt(n_0 / n_l); it is stabilised before it is coarsened.  Copied. */
+  const double* stab;
 } irk_problem;
 
 /* Build the solver for one problem, Butcher table and step h_t: copies M, F,

@@ -42,7 +42,8 @@ class IrkStats(C.Structure):
 
 class IrkProblem(C.Structure):
     _fields_ = [("M", IrkCsr), ("F", IrkCsr), ("g", c_double_p), ("n_nodes", C.c_int32),
-                ("n_tri", C.c_int32), ("xy", c_double_p), ("tri", c_int32_p), ("dof", c_int32_p)]
+                ("n_tri", C.c_int32), ("xy", c_double_p), ("tri", c_int32_p), ("dof", c_int32_p),
+                ("stab", c_double_p)]
 
 
 # (name, restype, argtypes) for every entry point of include/irk.h
@@ -61,6 +62,8 @@ SIGNATURES = [
     ("irk_fem_assemble_supg", C.c_int, [C.c_int32, c_double_p, C.c_int32, c_int32_p, C.c_double, c_double_p,
                                         c_double_p, c_double_p, C.c_double, c_int64_p, c_int64_p, c_int32_p,
                                         c_double_p, c_double_p, c_double_p]),
+    ("irk_fem_assemble_streamline", C.c_int, [C.c_int32, c_double_p, C.c_int32, c_int32_p, C.c_double,
+                                              c_double_p, c_int64_p, c_int32_p, c_double_p]),
     ("irk_setup", C.c_int, [C.POINTER(IrkProblem), C.POINTER(IrkButcher), C.c_double,
                             C.POINTER(IrkOptions), C.c_void_p, C.POINTER(C.c_void_p)]),
     ("irk_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(IrkStats)]),

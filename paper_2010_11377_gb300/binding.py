@@ -156,6 +156,20 @@ def irk_fem_assemble_supg(xy, tri, eps, wind, wind_c, ub=None, gamma=10.0):
     return rowptr, col, valM, valF, g
 
 
+def irk_fem_assemble_streamline(xy, tri, eps, wind_c, rowptr, col):
+    """Streamline-diffusion matrix of the coarse-level SUPG stabilisation on the
+    pattern (rowptr, col) of irk_fem_assemble_supg."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    wind_c = np.ascontiguousarray(wind_c, dtype=np.float64)
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    valT = np.zeros(col.size)
+    check(lib().irk_fem_assemble_streamline(xy.shape[0], _dp(xy), tri.shape[0], _ip(tri), float(eps), _dp(wind_c),
+                                            _lp(rowptr), _ip(col), _dp(valT)))
+    return valT
+
+
 # ---------------------------------------------------------------------------
 # context
 # ---------------------------------------------------------------------------
@@ -186,9 +200,11 @@ class Context:
         return self.handle
 
 
-def irk_setup(rowptr, col, valM, valF, butcher, h_t, options=None, g=None, mesh=None, stream=None) -> Context:
+def irk_setup(rowptr, col, valM, valF, butcher, h_t, options=None, g=None, mesh=None, stream=None,
+              stab=None) -> Context:
     """butcher = (A, b, c); mesh = dict(xy, tri, dof) or None; stream = a
-    torch.cuda.Stream (None: the current stream)."""
+    torch.cuda.Stream (None: the current stream); stab = the streamline
+    matrix's values on the pattern of M (coarse-level SUPG stabilisation) or None."""
     import torch
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
@@ -205,6 +221,12 @@ def irk_setup(rowptr, col, valM, valF, butcher, h_t, options=None, g=None, mesh=
         g = np.ascontiguousarray(g, dtype=np.float64)
         keep.append(g)
     prob.g = _dp(g)
+    if stab is not None:
+        stab = np.ascontiguousarray(stab, dtype=np.float64)
+        if stab.size != col.size:
+            raise ValueError("stab must hold one value per entry of the pattern of M")
+        keep.append(stab)
+    prob.stab = _dp(stab)
     n_tri = 0
     if mesh is not None:
         xy = np.ascontiguousarray(mesh["xy"], dtype=np.float64)

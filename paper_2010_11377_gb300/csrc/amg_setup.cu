@@ -594,6 +594,27 @@ static bool coarsen(Level& lev, int level, const AmgParams& p, CsrD& P, CsrD& R,
   return true;
 }
 
+// A += coef * T where the pattern of T lies inside that of A (both rows sorted);
+// an entry of T missing from A sets *bad
+__global__ void k_csr_add_subpattern(int n, const int* __restrict__ arp, const int* __restrict__ acol,
+                                     double* __restrict__ aval, const int* __restrict__ trp,
+                                     const int* __restrict__ tcol, const double* __restrict__ tval, double coef,
+                                     int* __restrict__ bad) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int k = arp[r];
+  const int ke = arp[r + 1];
+  for (int q = trp[r]; q < trp[r + 1]; ++q) {
+    const int c = tcol[q];
+    while (k < ke && acol[k] < c) ++k;
+    if (k == ke || acol[k] != c) {
+      atomicOr(bad, 1);
+      return;
+    }
+    aval[k] = __dadd_rn(aval[k], __dmul_rn(coef, tval[q]));
+  }
+}
+
 static void alloc_level_vectors(Level& L, int prec, DevPool& pool) {
   size_t es = (prec == 64) ? sizeof(double) : sizeof(float);
   size_t n = L.n > 0 ? L.n : 1;
@@ -604,7 +625,8 @@ static void alloc_level_vectors(Level& L, int prec, DevPool& pool) {
   L.d = pool.alloc(es * n);
 }
 
-void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaStream_t st) {
+void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaStream_t st, const CsrD* T0,
+               double c_stab) {
   H.amg_prec = p.amg_prec;
   H.lv.clear();
   H.lv.emplace_back();
@@ -613,12 +635,35 @@ void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaS
   H.lv[0].nnz = A0.nnz;
   int maxl = p.max_levels < MAX_LEVELS ? p.max_levels : MAX_LEVELS;
   int coarse_max = p.coarse_max < MAX_COARSE ? p.coarse_max : MAX_COARSE;
+  // coarse-level SUPG stabilisation: the projected streamline matrix of the
+  // current level and the mesh-size factor f of the level above
+  CsrD T = T0 ? *T0 : CsrD{};
+  double f_prev = 1.0;
   while (true) {
     Level& lev = H.lv.back();
     int l = static_cast<int>(H.lv.size()) - 1;
     if (lev.n <= coarse_max || static_cast<int>(H.lv.size()) >= maxl) break;
     CsrD P, R, Ac;
     if (!coarsen(lev, l, p, P, R, Ac, pool, st)) break;
+    if (T0) {
+      CsrD TP, Tc;
+      csr_spgemm(T, P, TP, pool, st);
+      csr_spgemm(R, TP, Tc, pool, st);
+      pool.release(TP.rowptr);
+      pool.release(TP.col);
+      pool.release(TP.val);
+      const double f = std::sqrt(double(A0.n) / double(Ac.n));
+      const double coef = c_stab * (f - f_prev);
+      Tmp tmp;
+      int* bad = tmp.get<int>(1);
+      CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+      k_csr_add_subpattern<<<nb(Ac.n), 256, 0, st>>>(Ac.n, Ac.rowptr, Ac.col, Ac.val, Tc.rowptr, Tc.col, Tc.val,
+                                                     coef, bad);
+      CK_LAUNCH();
+      if (rd(bad, st)) fail(IRK_ERR_INVALID, "streamline matrix pattern not inside the Galerkin pattern");
+      f_prev = f;
+      T = Tc;
+    }
     int pprec = p.amg_prec == 64 ? 64 : 32;
     make_matT(P, lev.Pm, pprec, pool, st);
     make_matT(R, lev.Rm, pprec, pool, st);

@@ -140,7 +140,9 @@ static void build_hierarchies(Ctx& c) {
     A0.col = c.Mc.col;
     A0.val = H.pool.get<double>(c.Mc.nnz > 0 ? c.Mc.nnz : 1);
     csr_axpby_same_pattern(c.Mc, c.Mc.val, c.Fc.val, coefs[q], A0.val, c.stream);
-    amg_build(H, A0, c.amg, H.pool, c.stream);
+    CsrD T0 = A0;
+    T0.val = c.Tval;
+    amg_build(H, A0, c.amg, H.pool, c.stream, c.Tval ? &T0 : nullptr, coefs[q]);
   }
 }
 
@@ -545,6 +547,10 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     irk::csr_to_sell(c.Mc, c.Ms, 1, 0, 0, c.pool, c.stream);
     irk::sell_share_pattern(c.Ms, c.Fc.val, c.Fc, c.Fs, 1, 1, c.pool, c.stream);
     irk::kron_split_build(c);
+    if (prob->stab) {
+      c.Tval = c.pool.get<double>(M.nnz > 0 ? M.nnz : 1);
+      if (M.nnz) CK(cudaMemcpy(c.Tval, prob->stab, sizeof(double) * M.nnz, cudaMemcpyHostToDevice));
+    }
     c.g = c.pool.get<double>(c.n);
     if (prob->g) CK(cudaMemcpy(c.g, prob->g, sizeof(double) * c.n, cudaMemcpyHostToDevice));
     else CK(cudaMemset(c.g, 0, sizeof(double) * c.n));

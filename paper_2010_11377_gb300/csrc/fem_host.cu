@@ -451,4 +451,51 @@ irk_status irk_fem_assemble_supg(int32_t n_nodes, const double* xy, int32_t n_tr
   return IRK_OK;
 }
 
+irk_status irk_fem_assemble_streamline(int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri,
+                                       double eps, const double* wind_c, const int64_t* rowptr,
+                                       const int32_t* col, double* valT) {
+  if (n_nodes <= 0 || n_tri <= 0 || !xy || !tri || !wind_c || !rowptr || !col || !valT || !(eps > 0.0)) {
+    irk::set_global_error("bad argument to irk_fem_assemble_streamline");
+    return IRK_ERR_INVALID;
+  }
+  for (int64_t e = 0; e < 3 * int64_t(n_tri); ++e)
+    if (tri[e] < 0 || tri[e] >= n_nodes) {
+      irk::set_global_error("triangle vertex out of range");
+      return IRK_ERR_INVALID;
+    }
+  std::fill(valT, valT + rowptr[n_nodes], 0.0);
+  for (int e = 0; e < n_tri; ++e) {
+    const int32_t* t = tri + 3 * e;
+    Geo geo;
+    if (!geometry(xy, t, geo)) {
+      irk::set_global_error("mesh triangles must be counter-clockwise and non-degenerate");
+      return IRK_ERR_INVALID;
+    }
+    const double wcx = wind_c[2 * e], wcy = wind_c[2 * e + 1];
+    double wcg[3], sum = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      wcg[a] = wcx * geo.gx[a] + wcy * geo.gy[a];
+      sum += std::fabs(wcg[a]);
+    }
+    const double wn = std::sqrt(wcx * wcx + wcy * wcy);
+    if (!(sum > 0.0 && wn > 0.0)) continue;
+    const double he = 2.0 * wn / sum;
+    if (!(wn * he / (2.0 * eps) > 1.0)) continue;   // Peclet number at most 1: no SUPG term
+    const double slope = he / (2.0 * wn);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const int i = t[a], j = t[b];
+        const int32_t* beg = col + rowptr[i];
+        const int32_t* end = col + rowptr[i + 1];
+        const int32_t* it = std::lower_bound(beg, end, j);
+        if (it == end || *it != j) {
+          irk::set_global_error("triangle entry missing from the given pattern");
+          return IRK_ERR_INVALID;
+        }
+        valT[it - col] += slope * geo.area * wcg[a] * wcg[b];
+      }
+  }
+  return IRK_OK;
+}
+
 }  // extern "C"

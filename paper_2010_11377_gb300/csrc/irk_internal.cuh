@@ -345,6 +345,7 @@ struct Ctx {
   Sell Ms, Fs;              // SELL-32: Ms.v64 = M, Fs.v64 = F (FP64), Fs.v32 = F (FP32)
   float4* MFs = nullptr;    // SELL-32 {M hi, M lo, F hi, F lo} single-float pairs, or null
   double* g = nullptr;      // lift (n)
+  double* Tval = nullptr;   // streamline matrix of the coarse-level SUPG stabilisation (pattern of Mc), or null
   bool symmetric = false;
 
   // mesh (optional)
@@ -433,7 +434,10 @@ void csr_copy_to_host(const CsrD& A, std::vector<int>& rp, std::vector<int>& col
                       std::vector<double>& val, cudaStream_t st);
 
 // AMG setup
-void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaStream_t st);
+// T0: streamline matrix of the coarse-level SUPG stabilisation on the pattern
+// of A0 (or null), c_stab: the block coefficient c of A0 = M + c F
+void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaStream_t st,
+               const CsrD* T0 = nullptr, double c_stab = 0.0);
 
 // V-cycle on hierarchy H: rhs in H.lv[0].b, result written to out (level-0 size,
 // V-cycle precision).  Returns the number of kernels launched.

@@ -6,7 +6,8 @@ import numpy as np
 
 import synth
 
-from .binding import irk_fem_assemble, irk_fem_assemble_p2, irk_fem_assemble_supg, irk_fem_quad_points
+from .binding import (irk_fem_assemble, irk_fem_assemble_p2, irk_fem_assemble_streamline, irk_fem_assemble_supg,
+                      irk_fem_quad_points)
 
 
 def heat(N: int, kappa=None) -> dict:
@@ -49,5 +50,6 @@ def double_glazing_supg(N: int, eps: float = 1.0 / 200.0, gamma: float = 10.0) -
     wind_c = synth.double_glazing_wind(cen[:, 0], cen[:, 1])
     ub = synth.double_glazing_boundary(mesh)
     rowptr, col, valM, valF, g = irk_fem_assemble_supg(mesh.xy, mesh.tri, eps, wind, wind_c, ub=ub, gamma=gamma)
+    valT = irk_fem_assemble_streamline(mesh.xy, mesh.tri, eps, wind_c, rowptr, col)
     return dict(kind="double_glazing_supg", N=N, n=mesh.n_nodes, mesh=mesh, rowptr=rowptr, col=col, valM=valM,
-                valF=valF, g=g, eps=eps, u0=ub.copy(), mesh_arrays=None)
+                valF=valF, g=g, eps=eps, u0=ub.copy(), mesh_arrays=None, valT=valT)

@@ -51,8 +51,11 @@ def oracle_ctx(prob, A, kind, h, amg_prec="f64", mesh=None, b=None, **opt):
     o = bnd.irk_default_options(kind="CUSTOM", amg_prec=amg_prec, **opt)
     o.Atilde = At_c.ctypes.data_as(bnd._abi.c_double_p)
     bw = A[-1].copy() if b is None else b
+    # a SUPG problem's streamline matrix (coarse-level stabilisation) on the same pattern
+    T = getattr(prob, "T", None)
+    stab = None if T is None else np.asarray(T.tocsr()[coo.row, coo.col]).ravel()
     ctx = bnd.irk_setup(M.indptr.astype(np.int64), M.indices, M.data, F.data,
-                        (A, bw, np.zeros(A.shape[0])), h, options=o, g=prob.g, mesh=mesh)
+                        (A, bw, np.zeros(A.shape[0])), h, options=o, g=prob.g, mesh=mesh, stab=stab)
     ctx._keep = At_c
     return ctx, At
 
@@ -415,6 +418,61 @@ def test_supg_nitsche_steps(prec, kind):
         if prec == "f64":
             assert _its_close(st["iterations"], amg_sol.step(refs[t]).iterations)
         u = out
+
+
+def test_supg_stabilised_hierarchy_parity():
+    """Coarse-level SUPG stabilisation: the library's hierarchy of a SUPG
+    double-glazing block (level 0 bit-identical, aggregates identical on every
+    level, stabilised coarse matrices within 1e-13 of the oracle's)."""
+    N, eps = 80, 0.005
+    mesh = synth.structured_mesh(N, "box")
+    prob = ofem.double_glazing_supg_nitsche(mesh, eps, synth.double_glazing_wind, synth.double_glazing_boundary(mesh))
+    A, _, _ = obt.radau_iia(2)
+    h = 1.0
+    opts = dict(theta=0.08, coarse_max=256, smoother="chebyshev", cheb_degree=4, cheb_lo=0.3)
+    ctx, At = oracle_ctx(prob, A, "LD", h, p_smooth=1, **opts)
+    for stage in range(2):
+        c = h * At[stage, stage]
+        Bk = (prob.M + c * prob.F).tocsr()
+        H = oamg.Hierarchy(Bk, p_smooth=1, stab=(prob.T, c), **opts)
+        Hplain = oamg.Hierarchy(Bk, p_smooth=1, **opts)
+        rows, _ = B().irk_amg_info(ctx, stage)
+        assert rows == H.sizes() and len(rows) >= 3
+        for l in range(1, len(rows)):
+            rp, col, val = B().irk_amg_level_matrix(ctx, stage, l)
+            Lg = sp.csr_matrix((val, col, rp), shape=(rows[l], rows[l]))
+            Lo = H.levels[l].A
+            assert abs(Lg - Lo).max() <= 1e-13 * abs(Lo).max()
+            if l + 1 < len(rows):
+                assert np.array_equal(B().irk_amg_aggregates(ctx, stage, l), H.levels[l].agg)
+        # the stabilisation changed the coarse operators
+        assert abs(H.levels[1].A - Hplain.levels[1].A).max() > 0.0
+
+
+def test_supg_convection_dominated_solve():
+    """The paper's double-glazing time-step table (Table 13) at h_x^-1 = 128,
+    eps = 0.005, s = 2, h_t = 1 (where the unstabilised V-cycle stops
+    contracting): the library with the coarse-level stabilisation and the
+    stronger smoother (Chebyshev degree 8 on [0.3, 1], V(2,2)) solves the
+    manufactured system with left GMRES to 1e-8, k within 1e-6 of k*, in as many
+    iterations as the oracle (within 10 %)."""
+    mesh = synth.structured_mesh(256, "box")
+    prob = ofem.double_glazing_supg_nitsche(mesh, 0.005, synth.double_glazing_wind,
+                                            synth.double_glazing_boundary(mesh))
+    A, b, _ = obt.radau_iia(2)
+    h = 1.0
+    opts = dict(cheb_lo=0.3, cheb_degree=8, nu_pre=2, nu_post=2, p_smooth=1)
+    ctx, At = oracle_ctx(prob, A, "LD", h, amg_prec="f64", b=b, side="left", rtol=1e-8, **opts)
+    kstar = synth.random_stage_block(prob.n, 2, 2128)
+    rhs = oirk.apply_operator(prob.M, prob.F, A, h, kstar)
+    k = torch.empty(2 * prob.n, dtype=torch.float64, device="cuda")
+    st = B().irk_solve(ctx, dev(rhs.ravel()), k)
+    assert np.linalg.norm(host(k).reshape(2, -1) - kstar) <= 1e-6 * np.linalg.norm(kstar)
+    pc = oirk.BlockPreconditioner(prob.M, prob.F, A, h, "LD", "amg", Atilde=At, amg_opts=opts, stab=prob.T)
+    ores = oirk.gmres_left(lambda z: oirk.apply_operator(prob.M, prob.F, A, h, z), pc.apply, rhs, rtol=1e-8)
+    assert ores.converged
+    assert _its_close(st["iterations"], ores.iterations), (st["iterations"], ores.iterations)
+    ctx.close()
 
 
 @pytest.mark.parametrize("side", ["right", "left"])
