@@ -126,8 +126,11 @@ class GmresResult:
         self.history = history
 
 
-def fgmres(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000):
+def fgmres(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000, record=None):
     """Solve A x = b from x0 = 0; stop when ||b - A x||_2 <= rtol ||b||_2.
+    ``record`` (a dict, tests only) receives the first cycle's V, Z, the
+    Hessenberg matrix before the Givens rotations, its width k and the final
+    residual estimate |g_k|.
 
     Each cycle: v_0 = r / ||r||; for j: z_j = P^{-1} v_j (stored, flexible),
     w = A z_j, MGS against v_0..v_j, Givens rotations on the Hessenberg
@@ -169,6 +172,8 @@ def fgmres(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000):
             H[j + 1, j] = np.linalg.norm(w)
             if H[j + 1, j] != 0.0:
                 V[j + 1] = w / H[j + 1, j]
+            if record is not None and restarts == 0:
+                record.setdefault("H", np.zeros((m + 1, m)))[:j + 2, j] = H[:j + 2, j]
             for i in range(j):
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
@@ -184,6 +189,8 @@ def fgmres(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000):
             k = j + 1
             if abs(g[j + 1]) <= rtol * bnorm or it >= max_it:
                 break
+        if record is not None and restarts == 0:
+            record.update(V=V[:k + 1].copy(), Z=Z[:k].copy(), k=k, estimate=abs(g[k]))
         y = np.zeros(k)
         for i in range(k - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
@@ -235,6 +242,8 @@ def gmres_left(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000):
             H[j + 1, j] = np.linalg.norm(w)
             if H[j + 1, j] != 0.0:
                 V[j + 1] = w / H[j + 1, j]
+            if record is not None and restarts == 0:
+                record.setdefault("H", np.zeros((m + 1, m)))[:j + 2, j] = H[:j + 2, j]
             for i in range(j):
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]

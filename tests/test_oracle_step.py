@@ -341,3 +341,31 @@ def test_c1_spectrum_and_final_state():
     for _ in range(20):
         u = sol.step(u, direct=True).u
     assert abs(np.linalg.norm(u) - 3.267e-8) < 0.001e-8
+
+
+def test_fgmres_arnoldi_relation():
+    """The flexible Arnoldi relation A Z_k = V_{k+1} Hbar_k of the first cycle
+    (before the Givens rotations) to 1e-12, an orthonormal basis (MGS), and the
+    Givens residual estimate |g_k| equal to the true residual of the cycle's
+    iterate (the least-squares solution over the recorded basis): the
+    definition of FGMRES, checked on a 14^2 heat step with the AMG
+    preconditioner (P^{-1} is then not the exact inverse)."""
+    mesh, prob = _heat(14)
+    A, b, _ = bt.radau_iia(3)
+    sol = irk.IRKSolver(prob, A, b, 0.05, kind="LD", subsolve="amg")
+    rhs = irk.stage_rhs(prob.F, prob.g, synth.heat_u0(mesh), 3)
+    rec = {}
+    res = irk.fgmres(sol.op, sol.pc.apply, rhs, m=30, rtol=1e-12, record=rec)
+    k, V, Z, H = rec["k"], rec["V"], rec["Z"], rec["H"][: rec["k"] + 1, : rec["k"]]
+    assert k >= 3 and res.converged
+    AZ = np.stack([sol.op(z.reshape(rhs.shape)).ravel() for z in Z], axis=1)
+    assert np.linalg.norm(AZ - V.T @ H) <= 1e-12 * np.linalg.norm(AZ)
+    # unit vectors; orthogonal to rounding while the Krylov basis is well
+    # conditioned (MGS loses orthogonality in proportion to its condition
+    # number as the cycle converges, without affecting the Arnoldi relation)
+    assert np.abs(np.linalg.norm(V, axis=1) - 1.0).max() <= 1e-14
+    assert np.abs(V[:2] @ V[:2].T - np.eye(2)).max() <= 1e-13
+    # the LS solution's true residual equals the estimate
+    y, *_ = np.linalg.lstsq(H, np.eye(k + 1)[:, 0] * np.linalg.norm(rhs), rcond=None)
+    r_true = np.linalg.norm(rhs.ravel() - AZ @ y)
+    assert abs(r_true - rec["estimate"]) <= 1e-9 * np.linalg.norm(rhs)
