@@ -242,8 +242,6 @@ def gmres_left(apply_A, apply_Pinv, b, m=30, rtol=1e-10, max_it=1000):
             H[j + 1, j] = np.linalg.norm(w)
             if H[j + 1, j] != 0.0:
                 V[j + 1] = w / H[j + 1, j]
-            if record is not None and restarts == 0:
-                record.setdefault("H", np.zeros((m + 1, m)))[:j + 2, j] = H[:j + 2, j]
             for i in range(j):
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
