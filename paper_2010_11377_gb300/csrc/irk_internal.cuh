@@ -126,7 +126,6 @@ struct Sell {               // SELL: slices of 32 / tpr rows, tpr threads per ro
   unsigned char* suni = nullptr;
   short* pdcol = nullptr;
   int64_t nnz_nonuni = 0;
-  int maxoff = -1;           // largest |column - row| of the stored entries (with dcol), else -1
   double* v64 = nullptr;
   float* v32 = nullptr;
   __nv_bfloat16* v16 = nullptr;

@@ -313,7 +313,7 @@ __global__ void k_sell_fill_vals(int n, int nslices, const int* __restrict__ row
 // 16-bit column offsets from the row; flag set if one does not fit
 __global__ void k_sell_offsets(int n, int nslices, int tpr, const int* __restrict__ rowptr,
                                const int64_t* __restrict__ sptr, const int* __restrict__ scol,
-                               short* __restrict__ dcol, int* __restrict__ overflow, int* __restrict__ maxabs) {
+                               short* __restrict__ dcol, int* __restrict__ overflow) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nslices * SELL_C) return;
   int sl, lane, r, q;
@@ -322,7 +322,6 @@ __global__ void k_sell_offsets(int n, int nslices, int tpr, const int* __restric
   int w = static_cast<int>((sptr[sl + 1] - base) / SELL_C);
   int len = r < n ? rowptr[r + 1] - rowptr[r] : 0;
   bool bad = false;
-  int mx = 0;
   for (int k = 0; k < w; ++k) {
     int64_t idx = base + int64_t(k) * SELL_C + lane;
     int d = (k * tpr + q) < len ? scol[idx] - r : 0;
@@ -330,11 +329,9 @@ __global__ void k_sell_offsets(int n, int nslices, int tpr, const int* __restric
       bad = true;
       d = 0;
     }
-    mx = max(mx, abs(d));
     dcol[idx] = static_cast<short>(d);
   }
   if (bad) atomicOr(overflow, 1);
-  atomicMax(maxabs, mx);
 }
 
 // one warp per SELL-32 slice: the slice shares one offset pattern when its 32
@@ -412,19 +409,15 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
     CK_LAUNCH();
   }
   S.dcol = nullptr;
-  S.maxoff = -1;
   if (ns > 0 && A.ncols == A.n && sell_offsets_enabled()) {
     short* dc = pool.get<short>(np);
     Tmp tmp;
-    int* ovf = tmp.get<int>(2);
-    CK(cudaMemsetAsync(ovf, 0, 2 * sizeof(int), st));
+    int* ovf = tmp.get<int>(1);
+    CK(cudaMemsetAsync(ovf, 0, sizeof(int), st));
     int nt = ns * SELL_C;
-    k_sell_offsets<<<(nt + 255) / 256, 256, 0, st>>>(A.n, ns, tpr, A.rowptr, S.sptr, S.col, dc, ovf, ovf + 1);
+    k_sell_offsets<<<(nt + 255) / 256, 256, 0, st>>>(A.n, ns, tpr, A.rowptr, S.sptr, S.col, dc, ovf);
     CK_LAUNCH();
-    if (read_scalar(ovf, st) == 0) {
-      S.dcol = dc;
-      S.maxoff = read_scalar(ovf + 1, st);
-    }
+    if (read_scalar(ovf, st) == 0) S.dcol = dc;
   }
   S.suni = nullptr;
   S.pdcol = nullptr;

@@ -11,7 +11,6 @@
 #include "irk_internal.cuh"
 
 #include <cmath>
-#include <cstdlib>
 
 namespace irk {
 
@@ -169,119 +168,6 @@ k_smooth(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T
   if (dout) dout[r] = d;
 }
 
-// ---------------------------------------------------------------------------
-// Tiled variants for large SELL-32 operators of small bandwidth (the finest
-// level: natural order, |column - row| <= maxoff): a block of TILE_ROWS rows
-// first stages the operand over rows [r0 - maxoff, r0 + TILE_ROWS + maxoff) in
-// shared memory with coalesced loads, then every row product gathers from
-// shared memory, so no thread waits on a chain of dependent global loads.
-// Same operand values and the same summation order as k_smooth / k_resid.
-// ---------------------------------------------------------------------------
-constexpr int TILE_ROWS = 1024;
-
-template <typename V, typename T, int XM>
-__device__ __forceinline__ void stage_tile(T* __restrict__ xs, int n, int r0, int H, const T* __restrict__ dinv,
-                                           const T* __restrict__ b, const T* __restrict__ xin, T beta0) {
-  const int span = TILE_ROWS + 2 * H;
-  for (int i = threadIdx.x; i < span; i += TILE_ROWS) {
-    const int c = r0 - H + i;
-    T v = T(0);
-    if (c >= 0 && c < n) v = (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : xin[c];
-    xs[i] = v;
-  }
-}
-
-template <typename V, typename T>
-__device__ __forceinline__ T tile_row_dot(const LMat<V>& A, int r, const T* __restrict__ xc) {
-  // xc points at the tile entry of row r itself
-  const int sl = r >> 5, ln = r & 31;
-  const int64_t base = A.sptr[sl];
-  const int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-  T acc = T(0);
-  if (A.suni && A.suni[sl]) {
-    const short* __restrict__ pd = A.pdcol + (base >> 5);
-    for (int k = 0; k < w; ++k)
-      acc = fma(widen(A.val[base + (int64_t(k) << 5) + ln]), xc[pd[k]], acc);
-  } else {
-    for (int k = 0; k < w; ++k) {
-      const int64_t idx = base + (int64_t(k) << 5) + ln;
-      acc = fma(widen(A.val[idx]), xc[A.dcol[idx]], acc);
-    }
-  }
-  return acc;
-}
-
-template <typename V, typename T, int XM>
-__global__ void __launch_bounds__(TILE_ROWS, 2)
-k_smooth_tiled(LMat<V> A, int H, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ xin,
-               const T* din, T* __restrict__ xout, T* dout, T alpha, T beta, T beta0, JPtr<T> out) {
-  extern __shared__ __align__(16) unsigned char tile_raw[];
-  T* xs = reinterpret_cast<T*>(tile_raw);
-  pdl_trigger();
-  pdl_wait();
-  const int r0 = blockIdx.x * TILE_ROWS;
-  if (XM != XM_ZERO) {
-    stage_tile<V, T, XM>(xs, A.n, r0, H, dinv, b, xin, beta0);
-    __syncthreads();
-  }
-  const int r = r0 + threadIdx.x;
-  if (r >= A.n) return;
-  T ax = T(0);
-  if (XM != XM_ZERO) ax = tile_row_dot<V, T>(A, r, xs + H + threadIdx.x);
-  T dr = dinv[r], br = b[r];
-  T xr, dprev;
-  if (XM == XM_EXPLICIT) {
-    xr = xin[r];
-    dprev = din ? din[r] : T(0);
-  } else if (XM == XM_IMPLICIT) {
-    xr = beta0 * dr * br;
-    dprev = xr;
-  } else {
-    xr = T(0);
-    dprev = T(0);
-  }
-  T res = dr * (br - ax);
-  T d = alpha * dprev + beta * res;
-  T xn = xr + d;
-  if (out.base) out.get()[r] = xn;
-  else xout[r] = xn;
-  if (dout) dout[r] = d;
-}
-
-template <typename V, typename T, int XM>
-__global__ void __launch_bounds__(TILE_ROWS, 2)
-k_resid_tiled(LMat<V> A, int H, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
-              T beta0, T* __restrict__ r_out) {
-  extern __shared__ __align__(16) unsigned char tile_raw[];
-  T* xs = reinterpret_cast<T*>(tile_raw);
-  pdl_trigger();
-  pdl_wait();
-  const int r0 = blockIdx.x * TILE_ROWS;
-  stage_tile<V, T, XM>(xs, A.n, r0, H, dinv, b, x, beta0);
-  __syncthreads();
-  const int r = r0 + threadIdx.x;
-  if (r >= A.n) return;
-  r_out[r] = b[r] - tile_row_dot<V, T>(A, r, xs + H + threadIdx.x);
-}
-
-// IRK_TILED=0: the finest-level products gather from global memory (A/B switch)
-static bool tiled_enabled() {
-  static int on = -1;
-  if (on < 0) {
-    const char* e = std::getenv("IRK_TILED");
-    on = (e && std::atoi(e) == 0) ? 0 : 1;
-  }
-  return on == 1;
-}
-
-// shared-memory bytes of the tiled kernels for operator m, or 0 if they do not apply
-template <typename T>
-static size_t tile_bytes(const MatT& m) {
-  if (!tiled_enabled() || m.lanes != 1 || !m.sell.dcol || m.sell.maxoff < 0 || m.n < 8 * TILE_ROWS) return 0;
-  const size_t b = size_t(TILE_ROWS + 2 * m.sell.maxoff) * sizeof(T);
-  return b <= 48 * 1024 ? b : 0;
-}
-
 // r = b - A x  (x explicit or the implicit first step)
 template <typename V, typename T, int L, int XM>
 __global__ void __launch_bounds__(256)
@@ -414,14 +300,6 @@ struct VCycle {
   template <typename V, int XM>
   void smooth(const Level& L, const T* xin, const T* din, T* xout, T* dout, int step, JPtr<T> out) {
     LMat<V> A = lmat<V>(L.Am);
-    if (size_t tb = tile_bytes<T>(L.Am)) {
-      launch_k(k_smooth_tiled<V, T, XM>, nblk(L.Am.n, TILE_ROWS), TILE_ROWS, tb, st, A, L.Am.sell.maxoff,
-               static_cast<const T*>(L.dinv), static_cast<const T*>(L.b), xin, din, xout, dout, T(sc.alpha[step]),
-               T(sc.beta[step]), T(sc.beta[0]), out);
-      ++launches;
-      count_matvec<V>(L, XM == XM_EXPLICIT ? (din ? 4 : 3) : 2, dout ? 2 : 1);
-      return;
-    }
     IRK_DISPATCH_L(L.Am.lanes, {
       launch_k(k_smooth<V, T, LN, XM>, grid_for(L.Am), 256, 0, st, A, static_cast<const T*>(L.dinv),
                                                            static_cast<const T*>(L.b), xin, din, xout, dout,
@@ -508,19 +386,7 @@ struct VCycle {
     }
     // ---- residual and restriction
     const T beta0 = T(sc.beta[0]);
-    if (p.nu_pre > 0 && tile_bytes<T>(L.Am)) {
-      LMat<V> A = lmat<V>(L.Am);
-      const T* dv = static_cast<const T*>(L.dinv);
-      const size_t tb = tile_bytes<T>(L.Am);
-      const unsigned g = nblk(L.Am.n, TILE_ROWS);
-      if (implicit)
-        launch_k(k_resid_tiled<V, T, XM_IMPLICIT>, g, TILE_ROWS, tb, st, A, L.Am.sell.maxoff, dv, b, nullptr, beta0,
-                 rb);
-      else
-        launch_k(k_resid_tiled<V, T, XM_EXPLICIT>, g, TILE_ROWS, tb, st, A, L.Am.sell.maxoff, dv, b, cur, beta0, rb);
-      ++launches;
-      count_matvec<V>(L, 2, 1);
-    } else if (p.nu_pre > 0) {
+    if (p.nu_pre > 0) {
       LMat<V> A = lmat<V>(L.Am);
       const T* dv = static_cast<const T*>(L.dinv);
       IRK_DISPATCH_L(L.Am.lanes, {
