@@ -249,7 +249,11 @@ typedef struct {
   const double* stab;
 } irk_problem;
 
-/* Build the solver for one problem, Butcher table and step h_t: copies M, F,
+/* Build the solver for one problem, Butcher table and step h_t: the stage
+ * system (I_s (x) M + h_t A (x) F) k = r of Section 4 (Eq. block_coeff_mtx)
+ * with the preconditioner P = I_s (x) M + h_t A~ (x) F of Section 4.2
+ * (Eq. PrecForm), one AMG V-cycle per diagonal-block subsolve (Sections 4.2
+ * and 5).  Copies M, F,
  * g (and the mesh) to the device, forms A~ (opt->kind), and builds on the GPU
  * one AMG hierarchy per distinct diagonal block M + h_t A~_jj F.  `stream` is
  * a cudaStream_t (NULL = legacy default stream); the library also creates a
@@ -384,6 +388,13 @@ irk_status irk_residual_norm_noalloc(irk_ctx* ctx, const double* d_k, const doub
 
 /* d_y = M d_x (n). */
 irk_status irk_apply_mass(irk_ctx* ctx, const double* d_x, double* d_y);
+
+/* The final-time misfit of the adjoint runs (the L2 misfit 1/2 (u - d)^T M (u - d)
+ * whose gradient the discrete adjoint propagates, Section 2 with the adjoint of
+ * the time loop): *d_value (a DEVICE double) = 1/2 (d_u - d_d)^T M (d_u - d_d),
+ * summed in a fixed order; d_grad (n, or NULL) = M (d_u - d_d), the misfit's
+ * gradient for symmetric M.  d_u, d_d: n. */
+irk_status irk_misfit(irk_ctx* ctx, const double* d_u, const double* d_d, double* d_grad, double* d_value);
 
 /* Hierarchy of diagonal block `stage`: *nlevels and, per level (up to 16),
  * rows[l] and nnz[l] (host arrays of 16). */

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("irk_fem_assemble_supg", C.c_int, [C.c_int32, c_double_p, C.c_int32, c_int32_p, C.c_double, c_double_p,
                                         c_double_p, c_double_p, C.c_double, c_int64_p, c_int64_p, c_int32_p,
                                         c_double_p, c_double_p, c_double_p]),
+    ("irk_misfit", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("irk_fem_assemble_streamline", C.c_int, [C.c_int32, c_double_p, C.c_int32, c_int32_p, C.c_double,
                                               c_double_p, c_int64_p, c_int32_p, c_double_p]),
     ("irk_setup", C.c_int, [C.POINTER(IrkProblem), C.POINTER(IrkButcher), C.c_double,

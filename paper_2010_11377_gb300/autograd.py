@@ -66,9 +66,10 @@ class MassMisfit(torch.autograd.Function):
     def forward(fctx, e, solver: Solver):
         e = e.detach().contiguous()
         Me = torch.empty_like(e)
-        B.irk_apply_mass(solver.ctx, e, Me)
+        value = torch.empty(1, dtype=torch.float64, device=e.device)
+        B.irk_misfit(solver.ctx, e, torch.zeros_like(e), value, grad=Me)
         fctx.save_for_backward(Me)
-        return 0.5 * torch.dot(e, Me)
+        return value[0]
 
     @staticmethod
     def backward(fctx, g):

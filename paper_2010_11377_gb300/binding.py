@@ -385,6 +385,12 @@ def irk_apply_mass(ctx: Context, x, y):
     check(lib().irk_apply_mass(ctx.ptr, _dev(x), _dev(y)), ctx.ptr)
 
 
+def irk_misfit(ctx: Context, u, d, value, grad=None):
+    """value (one-element FP64 CUDA tensor) = 1/2 (u - d)^T M (u - d); grad
+    (n, or None) = M (u - d)."""
+    check(lib().irk_misfit(ctx.ptr, _dev(u), _dev(d), _dev(grad), _dev(value)), ctx.ptr)
+
+
 def irk_amg_info(ctx: Context, stage):
     nl = C.c_int32(0)
     rows = np.zeros(16, dtype=np.int32)

@@ -835,6 +835,17 @@ irk_status irk_apply_mass(irk_ctx* h, const double* d_x, double* d_y) {
   });
 }
 
+irk_status irk_misfit(irk_ctx* h, const double* d_u, const double* d_d, double* d_grad, double* d_value) {
+  if (!h || !d_u || !d_d || !d_value) return set_err(h, IRK_ERR_INVALID, "NULL argument");
+  return guarded(h, [&] {
+    Ctx& c = h->c;
+    irk::begin_call(c);
+    irk::misfit_launch(c, d_u, d_d, d_grad, d_value, c.stream);
+    c.launches += 2;
+    irk::end_call(c);
+  });
+}
+
 static const irk::Hier* hier_of(Ctx& c, int stage) {
   if (stage < 0 || stage >= c.s) irk::fail(IRK_ERR_INVALID, "stage out of range");
   int pos = 0;

@@ -476,6 +476,7 @@ void stage_update_launch(Ctx& c, double* u, cudaStream_t st);
 void record_launch(Ctx& c, cudaStream_t st);
 void kron_apply_plain(Ctx& c, const double* z, double* w, bool transpose, cudaStream_t st);
 void mass_apply_launch(Ctx& c, const double* x, double* y, cudaStream_t st);
+void misfit_launch(Ctx& c, const double* u, const double* d, double* grad, double* out, cudaStream_t st);
 void adjoint_lambda_launch(Ctx& c, const double* lam_in, double* lam_out, cudaStream_t st);
 void adjoint_grad_launch(Ctx& c, const double* u_n, const double* k_n, double* grad, cudaStream_t st);
 void adjoint_grad_launch_at(Ctx& c, const double* u_base, const double* k_base, const int* step, double* grad,

@@ -1026,6 +1026,42 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int count, d
   *out = sqrt(s);
 }
 
+// misfit 1/2 (u - d)^T M (u - d): per-block partial sums of (u - d)_r (M (u - d))_r
+// (deterministic order), and M (u - d) when grad is given
+__global__ void __launch_bounds__(BS)
+k_misfit_partials(int n, SellView<double> Mv, const double* __restrict__ u, const double* __restrict__ d,
+                  double* __restrict__ grad, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int r = blockIdx.x * BS + threadIdx.x; r < n; r += gridDim.x * BS) {
+    int sl = r >> 5, lane = r & 31;
+    int64_t base = Mv.sptr[sl];
+    int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
+    double me = 0.0;
+    for (int q = 0; q < wdt; ++q) {
+      int64_t idx = base + (int64_t(q) << 5) + lane;
+      int c = sell_col(Mv.col, Mv.dcol, idx, r);
+      me = fma(Mv.val[idx], u[c] - d[c], me);
+    }
+    if (grad) grad[r] = me;
+    acc = fma(u[r] - d[r], me, acc);
+  }
+  double v[1] = {acc};
+  block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+__global__ void k_half_sum(const double* __restrict__ partials, int count, double* __restrict__ out) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s = 0.0;
+  for (int q = 0; q < count; ++q) s += partials[q];
+  *out = 0.5 * s;
+}
+
+void misfit_launch(Ctx& c, const double* u, const double* d, double* grad, double* out, cudaStream_t st) {
+  k_misfit_partials<<<c.gs_grid, BS, 0, st>>>(c.n, view<double>(c.Ms), u, d, grad, c.partials);
+  k_half_sum<<<1, 32, 0, st>>>(c.partials, c.gs_grid, out);
+  CK_LAUNCH();
+}
+
 void residual_norm_launch(Ctx& c, const double* k, const double* b, double* partials, int grid, double* out,
                           cudaStream_t st) {
   IRK_DISPATCH_S(c.s, {

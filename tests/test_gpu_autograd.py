@@ -52,3 +52,29 @@ def test_autograd_matches_oracle_adjoint():
     glog = gk * kap
     assert np.linalg.norm(lk.grad.cpu().numpy() - glog) <= 1e-8 * np.linalg.norm(glog)
     ctx.close()
+
+
+def test_misfit_entry_point():
+    """irk_misfit against the oracle's misfit 1/2 (u - d)^T M (u - d) (FP64
+    sum-order rounding) and its gradient M (u - d)."""
+    from paper_2010_11377_gb300 import binding as B
+    from paper_2010_11377_gb300 import problems
+    N = 37
+    mesh = synth.structured_mesh(N)
+    prob = ofem.heat_problem(mesh)
+    p = problems.heat(N)
+    At, bt, ct = B.irk_butcher_table("radau_iia", 2)
+    ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (At, bt, ct), 0.05)
+    u = synth.random_smooth_u0(mesh, seed=3)
+    d = 0.5 * synth.random_smooth_u0(mesh, seed=4)
+    ref = oirk.misfit(prob.M, u, d)
+    value = torch.empty(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty(mesh.n, dtype=torch.float64, device="cuda")
+    ud = torch.tensor(u, device="cuda")
+    dd = torch.tensor(d, device="cuda")
+    B.irk_misfit(ctx, ud, dd, value, grad=grad)
+    assert abs(value.item() - ref) <= 1e-13 * abs(ref)
+    assert np.abs(grad.cpu().numpy() - prob.M @ (u - d)).max() <= 1e-14 * np.abs(prob.M @ (u - d)).max()
+    B.irk_misfit(ctx, ud, dd, value)           # without the gradient
+    assert abs(value.item() - ref) <= 1e-13 * abs(ref)
+    ctx.close()
