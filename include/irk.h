@@ -416,11 +416,13 @@ irk_status irk_amg_level_matrix(irk_ctx* ctx, int32_t stage, int32_t level, int6
  * loop), IRK_PROF_VCYCLE (one V-cycle on the first diagonal block),
  * IRK_PROF_PRECOND (the whole P^{-1} application), IRK_PROF_GS_DOTS and
  * IRK_PROF_GS_AXPY (the two Gram-Schmidt passes at basis index j),
- * IRK_PROF_SMOOTH0 (one finest-level Chebyshev step of the first block).
+ * IRK_PROF_SMOOTH0 (one finest-level Chebyshev step of the first block),
+ * IRK_PROF_VCYCLE_FROM (the part of a V-cycle of the first block from level j
+ * (>= 1) down: its smoothing, restrictions, coarsest solve and prolongations).
  * *ms receives the mean time per replay, *bytes the algorithmic DRAM bytes
  * of one replay and *flops its algorithmic floating-point operations. */
 enum { IRK_PROF_KRON = 0, IRK_PROF_VCYCLE = 1, IRK_PROF_PRECOND = 2, IRK_PROF_GS_DOTS = 3,
-       IRK_PROF_GS_AXPY = 4, IRK_PROF_SMOOTH0 = 5 };
+       IRK_PROF_GS_AXPY = 4, IRK_PROF_SMOOTH0 = 5, IRK_PROF_VCYCLE_FROM = 6 };
 irk_status irk_profile(irk_ctx* ctx, int32_t which, int32_t j, int32_t warm, int32_t reps, double* ms,
                        double* bytes, double* flops);
 

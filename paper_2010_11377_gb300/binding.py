@@ -415,7 +415,8 @@ def irk_amg_level_matrix(ctx: Context, stage, level):
     return rp, col, val
 
 
-PROFILE_TARGETS = {"kron": 0, "vcycle": 1, "precond": 2, "gs_dots": 3, "gs_axpy": 4, "smooth0": 5}
+PROFILE_TARGETS = {"kron": 0, "vcycle": 1, "precond": 2, "gs_dots": 3, "gs_axpy": 4, "smooth0": 5,
+                   "vcycle_from": 6}
 
 
 def irk_profile(ctx: Context, which: str, j: int = 0, warm: int = 3, reps: int = 20) -> dict:

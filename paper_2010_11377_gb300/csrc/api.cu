@@ -946,6 +946,12 @@ irk_status irk_profile(irk_ctx* h, int32_t which, int32_t j, int32_t warm, int32
         Fl = axpy ? 2.0 * (j + 2) * N : 2.0 * (j + 2) * N;
         break;
       }
+      case IRK_PROF_VCYCLE_FROM: {
+        // j = the first level (>= 1) of the partial V-cycle
+        irk::vcycle_launch_from(H0, c.amg, c.sc, j, c.stream, &B, &Fl);
+        launch = [&] { irk::vcycle_launch_from(H0, c.amg, c.sc, j, c.stream); };
+        break;
+      }
       case IRK_PROF_SMOOTH0: {
         irk::smooth0_launch(H0, c.amg, c.sc, c.stream, &B, &Fl);
         launch = [&] {

@@ -444,6 +444,8 @@ void amg_build(Hier& H, const CsrD& A0, const AmgParams& p, DevPool& pool, cudaS
 int vcycle_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, void* out_base,
                   const int* jp, int64_t jstride, int64_t off, cudaStream_t st, double* bytes = nullptr,
                   double* flops = nullptr);
+int vcycle_launch_from(const Hier& H, const AmgParams& p, const SmoothCoef& sc, int l0, cudaStream_t st,
+                       double* bytes = nullptr, double* flops = nullptr);
 void smooth0_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, cudaStream_t st, double* bytes,
                     double* flops);
 

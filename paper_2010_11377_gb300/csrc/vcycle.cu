@@ -466,6 +466,28 @@ int vcycle_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, void*
   return run_vcycle<float, float>(H, p, sc, o, st, bytes, flops);
 }
 
+// the part of one V-cycle from level l0 >= 1 down (on that level's buffers)
+int vcycle_launch_from(const Hier& H, const AmgParams& p, const SmoothCoef& sc, int l0, cudaStream_t st,
+                       double* bytes, double* flops) {
+  if (l0 < 1 || l0 >= static_cast<int>(H.lv.size())) fail(IRK_ERR_INVALID, "start level out of range");
+  int launches = 0;
+  if (H.amg_prec == 64) {
+    VCycle<double, double> vc{H, p, sc, st, 0, Cost{}};
+    vc.template level<double>(l0, jptr<double>(nullptr));
+    launches = vc.launches;
+    if (bytes) *bytes += vc.cost.bytes;
+    if (flops) *flops += vc.cost.flops;
+  } else {
+    VCycle<float, float> vc{H, p, sc, st, 0, Cost{}};
+    vc.template level<float>(l0, jptr<float>(nullptr));
+    launches = vc.launches;
+    if (bytes) *bytes += vc.cost.bytes;
+    if (flops) *flops += vc.cost.flops;
+  }
+  CK_LAUNCH();
+  return launches;
+}
+
 // one explicit finest-level smoothing step (step index 1) of hierarchy H
 void smooth0_launch(const Hier& H, const AmgParams& p, const SmoothCoef& sc, cudaStream_t st, double* bytes,
                     double* flops) {
