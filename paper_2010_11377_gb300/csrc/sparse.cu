@@ -486,14 +486,14 @@ int choose_lanes(int64_t nnz, int n) {
 
 // ---------------------------------------------------------------------------
 // Layout autotuner: for an operator of a given shape class (log2 of the rows,
-// log2 of the mean row length, precision) time y = A x with every candidate
+// log2 of the mean row length, precision, square or not) time y = A x with every candidate
 // thread tile (SELL thread-per-row, sliced SELL with 2, 4 or 8 threads per row,
 // or CSR with 2..32 lanes per row) and keep the fastest.  Decisions are cached for the process, so repeated set-ups
 // (batches, kappa updates) reuse them.  IRK_AUTOTUNE=0 uses the row-length rule.
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;
+std::map<std::tuple<int, int, int, int>, int> g_tune;
 
 int ilog2(double v) {
   int k = 0;
@@ -529,7 +529,9 @@ int autotune_lanes(const CsrD& A, int prec, cudaStream_t st) {
   int heuristic = choose_lanes(A.nnz, A.n);
   if (!autotune_enabled() || A.n < 64 || A.nnz == 0) return heuristic;
   double avg = double(A.nnz) / A.n;
-  auto key = std::make_tuple(ilog2(A.n), ilog2(avg * 2.0), prec);
+  // square operators (level matrices, 16-bit offsets possible) and rectangular
+  // ones (prolongation, restriction) are tuned separately
+  auto key = std::make_tuple(ilog2(A.n), ilog2(avg * 2.0), prec, A.ncols == A.n ? 1 : 0);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
