@@ -54,8 +54,8 @@ class BlockPreconditioner:
     V-cycle on the block (``subsolve='amg'``); ``stab`` (a SUPG problem's
     streamline matrix T) stabilises the coarse AMG levels of the block
     M + h A~_jj F with c = h A~_jj.
-    ``transpose=True`` applies P^T (for symmetric M, F: I (x) M + h A~^T (x) F,
-    whose substitution runs in the opposite direction).
+    ``transpose=True`` applies P^T = I (x) M^T + h A~^T (x) F^T, whose
+    substitution runs in the opposite direction with the transposed blocks.
     """
 
     def __init__(self, M, F, A, h, kind="LD", subsolve="amg", Atilde=None,
@@ -68,6 +68,8 @@ class BlockPreconditioner:
             direction = {"diag": "diag", "forward": "backward",
                          "backward": "forward"}[direction]
         self.direction = direction
+        if transpose:
+            M, F = M.T.tocsr(), F.T.tocsr()
         self.M, self.F, self.h = M, F, h
         self.s = self.At.shape[0]
         self.subsolve = subsolve

@@ -154,10 +154,59 @@ static void destroy_graphs(Ctx& c) {
   }
 }
 
+// adjoint work of a nonsymmetric problem runs on the transposed matrices and
+// hierarchies: swap them in for the scope (graphs capture the pointers)
+static void swap_transposed(Ctx& c) {
+  std::swap(c.Mc, c.tr.Mc);
+  std::swap(c.Fc, c.tr.Fc);
+  std::swap(c.Ms, c.tr.Ms);
+  std::swap(c.Fs, c.tr.Fs);
+  std::swap(c.MFs, c.tr.MFs);
+  c.hiers.swap(c.tr.hiers);
+}
+
+static void ensure_transposed(Ctx& c) {
+  if (c.tr.built) return;
+  CsrD Mt, Ft;
+  csr_transpose(c.Mc, Mt, c.pool, c.stream);
+  csr_transpose(c.Fc, Ft, c.pool, c.stream);   // the same pattern as Mt: M and F share one
+  c.tr.Mc = Mt;
+  c.tr.Fc = Ft;
+  c.tr.Fc.rowptr = Mt.rowptr;
+  c.tr.Fc.col = Mt.col;
+  csr_to_sell(Mt, c.tr.Ms, 1, 0, 0, c.pool, c.stream);
+  sell_share_pattern(c.tr.Ms, Ft.val, Ft, c.tr.Fs, 1, 1, c.pool, c.stream);
+  swap_transposed(c);
+  try {
+    kron_split_build(c);
+    build_hierarchies(c);
+  } catch (...) {
+    swap_transposed(c);
+    throw;
+  }
+  swap_transposed(c);
+  c.tr.built = true;
+}
+
+struct AdjointView {
+  Ctx& c;
+  bool on;
+  AdjointView(Ctx& c_, bool adjoint) : c(c_), on(adjoint && !c_.symmetric) {
+    if (on) {
+      ensure_transposed(c);
+      swap_transposed(c);
+    }
+  }
+  ~AdjointView() {
+    if (on) swap_transposed(c);
+  }
+};
+
 // One time-step graph (forward: rhs from c.u, update c.u; adjoint: rhs from
 // c.lam, lambda update into c.tmpn).  The FGMRES loop is a WHILE node whose
 // condition the last kernel of each iteration sets from the device state.
 static void build_graph(Ctx& c, bool adjoint) {
+  AdjointView av(c, adjoint);
   Graph& G = c.graph[adjoint ? 1 : 0];
   if (G.exec || c.host_loop) return;
   cudaStream_t st = c.stream;
@@ -220,6 +269,7 @@ static void build_graph(Ctx& c, bool adjoint) {
 // One solve: the step graph, or (host loop) the same kernel sequence with the
 // loop condition read back on the host after every iteration.
 static void launch_solve(Ctx& c, bool adjoint) {
+  AdjointView av(c, adjoint);
   Graph& G = c.graph[adjoint ? 1 : 0];
   if (!c.host_loop) {
     CK(cudaGraphLaunch(G.exec, c.stream));
@@ -314,7 +364,6 @@ static irk_status adjoint_one(Ctx& c, const double* lam_in, const double* u_n, c
 
 static void check_adjoint_ok(Ctx& c, bool need_grad) {
   if (c.side != 0) fail(IRK_ERR_INVALID, "the adjoint runs right-preconditioned contexts only (side = 0)");
-  if (!c.symmetric) fail(IRK_ERR_INVALID, "adjoint needs symmetric M and F (transposed hierarchies are not built)");
   if (need_grad && c.n_tri == 0) fail(IRK_ERR_INVALID, "kappa gradient needs the mesh in irk_setup");
 }
 
@@ -753,6 +802,11 @@ irk_status irk_set_kappa(irk_ctx* h, const double* d_kappa) {
     irk::kron_split_build(c);
     irk::destroy_graphs(c);
     irk::build_hierarchies(c);
+    if (c.tr.built) {   // the transposed problem follows F
+      for (auto& H : c.tr.hiers) H.pool.free_all();
+      c.tr.hiers.clear();
+      c.tr = irk::Ctx::Transposed{};
+    }
     irk::end_call(c);
   });
 }
@@ -783,7 +837,7 @@ irk_status irk_apply_precond(irk_ctx* h, const double* d_v, double* d_z, int32_t
   if (!h || !d_v || !d_z) return set_err(h, IRK_ERR_INVALID, "NULL argument");
   return guarded(h, [&] {
     Ctx& c = h->c;
-    if (transpose && !c.symmetric) irk::fail(IRK_ERR_INVALID, "transposed preconditioner needs symmetric M and F");
+    irk::AdjointView av(c, transpose != 0);
     irk::begin_call(c);
     irk::PrecondArgs pa{d_v, nullptr, 0, nullptr, c.Z, 0, nullptr};
     c.launches += irk::precond_launch(c, pa, transpose != 0, c.stream);
@@ -996,6 +1050,7 @@ void irk_destroy(irk_ctx* h) {
   if (c.stream) cudaStreamSynchronize(c.stream);
   irk::destroy_graphs(c);
   for (auto& H : c.hiers) H.pool.free_all();
+  for (auto& H : c.tr.hiers) H.pool.free_all();
   c.pool.free_all();
   if (c.ev_a) cudaEventDestroy(c.ev_a);
   if (c.ev_b) cudaEventDestroy(c.ev_b);

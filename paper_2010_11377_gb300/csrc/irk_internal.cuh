@@ -366,6 +366,16 @@ struct Ctx {
   AmgParams amg;
   SmoothCoef sc;
   std::vector<Hier> hiers;
+  // the transposed problem for the adjoint of nonsymmetric M and F (M^T, F^T on
+  // one pattern, their pair copy and the hierarchies of the blocks (M + c F)^T),
+  // built on first use and swapped in while adjoint work is launched
+  struct Transposed {
+    bool built = false;
+    CsrD Mc, Fc;
+    Sell Ms, Fs;
+    float4* MFs = nullptr;
+    std::vector<Hier> hiers;
+  } tr;
   irk_options opt;
 
   // FGMRES storage

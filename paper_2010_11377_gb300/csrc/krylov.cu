@@ -653,7 +653,7 @@ k_spmv64(int n, SellView<double> A, const double* __restrict__ x, double* __rest
   }
 }
 
-// lambda_n = lambda_{n+1} - F^T sum_i mu_i   (F symmetric)
+// lambda_n = lambda_{n+1} - F^T sum_i mu_i   (Fv: F^T, or F when F is symmetric)
 template <int S>
 __global__ void __launch_bounds__(BS)
 k_adj_lambda(int n, SellView<double> Fv, const double* __restrict__ mu, const double* __restrict__ lin,

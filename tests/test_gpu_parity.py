@@ -695,6 +695,47 @@ def test_edge_cases():
         bnd.irk_vcycle(ctx, 9, z, out)
 
 
+def test_adjoint_nonsymmetric():
+    """Double glazing (F = eps K + C nonsymmetric): the transposed
+    preconditioner against the oracle's P^T, one adjoint step against the
+    oracle's exact transposed stage solve, and dL/du0 of the checkpointed
+    reverse sweep against the oracle's discrete adjoint with exact solves."""
+    mesh, prob = dg(24)
+    A, b, _ = obt.radau_iia(3)
+    h, nsteps, every = 0.05, 4, 2
+    ctx, At = oracle_ctx(prob, A, "LD", h, amg_prec="f64", b=b, **AMG_OPTS)
+    bnd = B()
+    v = synth.random_stage_block(prob.n, 3, 11)
+    pc = oirk.BlockPreconditioner(prob.M, prob.F, A, h, "LD", "amg", Atilde=At, amg_opts=oracle_amg_opts(),
+                                  transpose=True)
+    z = torch.empty(3 * prob.n, dtype=torch.float64, device="cuda")
+    bnd.irk_apply_precond(ctx, dev(v.ravel()), z, transpose=True)
+    ref = pc.apply(v)
+    assert np.linalg.norm(host(z).reshape(3, -1) - ref) <= 1e-12 * np.linalg.norm(ref)
+    sol = oirk.IRKSolver(prob, A, b, h, kind="LD", subsolve="direct")
+    lam1 = synth.random_smooth_u0(mesh, seed=5)
+    ref_lam, _ = sol.adjoint_step(lam1, direct=True)
+    out = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    st = bnd.irk_adjoint_step(ctx, dev(lam1), None, None, out)
+    assert st["resid"] <= 1e-10
+    assert np.linalg.norm(host(out) - ref_lam) <= 1e-8 * np.linalg.norm(ref_lam)
+    # checkpointed sweep: dL/du0 for L = 1/2 (u_N - d)^T M (u_N - d)
+    u0 = synth.random_smooth_u0(mesh, seed=6)
+    d = 0.5 * u0
+    us, _ = sol.run(u0, nsteps, direct=True)
+    lam = prob.M @ (us[-1] - d)
+    for _ in range(nsteps):
+        lam, _ = sol.adjoint_step(lam, direct=True)
+    uN = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    ck = torch.empty(nsteps // every, prob.n, dtype=torch.float64, device="cuda")
+    bnd.irk_run(ctx, dev(u0), nsteps, uN, ckpt=ck, ckpt_every=every)
+    g = torch.empty_like(uN)
+    bnd.irk_apply_mass(ctx, uN - dev(d), g)
+    bnd.irk_adjoint_run(ctx, ck, nsteps, every, g, None)
+    assert np.linalg.norm(host(g) - lam) <= 1e-8 * np.linalg.norm(lam)
+    ctx.close()
+
+
 def test_adjoint_gradients():
     """Checkpointed adjoint (C ABI) vs the oracle's discrete adjoint with exact
     solves: dL/du0 and dL/dkappa to 1e-8."""

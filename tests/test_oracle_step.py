@@ -111,6 +111,25 @@ def test_preconditioner_substitution_is_exact(kind):
         assert np.max(np.abs(w - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("kind", ["J", "GSL", "DU", "LD"])
+def test_transposed_preconditioner_nonsymmetric(kind):
+    """The transposed preconditioner of a nonsymmetric problem (double glazing,
+    F = eps K + C) with exact subsolves equals the dense solve with the
+    transpose of P = I (x) M + h A~ (x) F."""
+    mesh = synth.structured_mesh(6, "box")
+    prob = fem.double_glazing_problem(mesh, 1 / 200, synth.double_glazing_wind,
+                                      synth.double_glazing_boundary(mesh))
+    assert abs(prob.F - prob.F.T).max() > 0.0
+    A, _, _ = bt.radau_iia(3)
+    h = 0.2
+    v = synth.random_stage_block(prob.n, 3, 2)
+    pc = irk.BlockPreconditioner(prob.M, prob.F, A, h, kind, "direct", transpose=True)
+    P = irk.kron_matrix(prob.M, prob.F, bt.atilde(A, kind), h).toarray()
+    ref = np.linalg.solve(P.T, v.ravel()).reshape(v.shape)
+    w = pc.apply(v)
+    assert np.max(np.abs(w - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
 def test_spectral_identity():
     """eig(P^{-1} A) = U_lambda eig((I + h lam A~)^{-1}(I + h lam A)) over the
     generalised eigenvalues lam of (F, M): brute force on a tiny mesh."""
