@@ -156,7 +156,7 @@ static void destroy_graphs(Ctx& c) {
 
 // adjoint work of a nonsymmetric problem runs on the transposed matrices and
 // hierarchies: swap them in for the scope (graphs capture the pointers)
-static void swap_transposed(Ctx& c) {
+void swap_transposed(Ctx& c) {
   std::swap(c.Mc, c.tr.Mc);
   std::swap(c.Fc, c.tr.Fc);
   std::swap(c.Ms, c.tr.Ms);
@@ -165,7 +165,7 @@ static void swap_transposed(Ctx& c) {
   c.hiers.swap(c.tr.hiers);
 }
 
-static void ensure_transposed(Ctx& c) {
+void ensure_transposed(Ctx& c) {
   if (c.tr.built) return;
   CsrD Mt, Ft;
   csr_transpose(c.Mc, Mt, c.pool, c.stream);
@@ -187,20 +187,6 @@ static void ensure_transposed(Ctx& c) {
   swap_transposed(c);
   c.tr.built = true;
 }
-
-struct AdjointView {
-  Ctx& c;
-  bool on;
-  AdjointView(Ctx& c_, bool adjoint) : c(c_), on(adjoint && !c_.symmetric) {
-    if (on) {
-      ensure_transposed(c);
-      swap_transposed(c);
-    }
-  }
-  ~AdjointView() {
-    if (on) swap_transposed(c);
-  }
-};
 
 // One time-step graph (forward: rhs from c.u, update c.u; adjoint: rhs from
 // c.lam, lambda update into c.tmpn).  The FGMRES loop is a WHILE node whose

@@ -170,8 +170,8 @@ irk_status irk_batch_create(irk_ctx* const* ctxs, int32_t count, int32_t nsteps,
       if (!ctxs[q] || ctxs[q]->c.device != dev) irk::fail(IRK_ERR_INVALID, "all batch contexts must share one device");
       if (!d_u0[q] || !d_uN[q] || !d_ckpt[q]) irk::fail(IRK_ERR_INVALID, "NULL instance buffer");
       if (ctxs[q]->c.side != 0) irk::fail(IRK_ERR_INVALID, "batches run right-preconditioned contexts only");
-      if (d_lambda && (!ctxs[q]->c.symmetric || (d_grad_kappa && d_grad_kappa[q] && ctxs[q]->c.n_tri == 0)))
-        irk::fail(IRK_ERR_INVALID, "adjoint instances need symmetric M, F (and the mesh for kappa gradients)");
+      if (d_lambda && d_grad_kappa && d_grad_kappa[q] && ctxs[q]->c.n_tri == 0)
+        irk::fail(IRK_ERR_INVALID, "kappa gradients of an instance need its mesh");
     }
     CK(cudaSetDevice(dev));
     CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
@@ -247,7 +247,11 @@ irk_status irk_batch_create(irk_ctx* const* ctxs, int32_t count, int32_t nsteps,
           cudaGraphConditionalHandle ha;
           cudaGraph_t abody;
           deps = B.add_while(b->gadj, deps, &ha, &abody);
-          auto ad = B.solve(c, true, abody, {});
+          std::vector<cudaGraphNode_t> ad;
+          {
+            irk::AdjointView av(c, true);   // nonsymmetric instances: transposed matrices and hierarchies
+            ad = B.solve(c, true, abody, {});
+          }
           B.capture(abody, ad, [&](cudaStream_t s) {
             if (grad) irk::adjoint_grad_launch_at(c, I.ustore, I.kstore, I.step, grad, s);
             irk::k_copy<<<grid_n(c.n), 256, 0, s>>>(c.lam, c.tmpn, c.n);

@@ -496,6 +496,26 @@ void adjoint_grad_launch_at(Ctx& c, const double* u_base, const double* k_base, 
 void assemble_kappa_launch(Ctx& c, const double* kappa, double* Fval, cudaStream_t st);
 void convert_launch(const void* in, int in_prec, void* out, int out_prec, int64_t n, cudaStream_t st);
 void profile_kron_launch(Ctx& c, cudaStream_t st);
+// the transposed problem of a nonsymmetric context (built on first use) and a
+// scope that swaps it in while adjoint work is launched or captured
+void ensure_transposed(Ctx& c);
+void swap_transposed(Ctx& c);
+struct AdjointView {
+  Ctx& c;
+  bool on;
+  AdjointView(Ctx& c_, bool adjoint) : c(c_), on(adjoint && !c_.symmetric) {
+    if (on) {
+      ensure_transposed(c);
+      swap_transposed(c);
+    }
+  }
+  ~AdjointView() {
+    if (on) swap_transposed(c);
+  }
+  AdjointView(const AdjointView&) = delete;
+  AdjointView& operator=(const AdjointView&) = delete;
+};
+
 // threads (= rows per grid-stride pass) per block of the outer Krylov kernels
 constexpr int OUTER_BLOCK = 256;
 void residual_norm_launch(Ctx& c, const double* k, const double* b, double* partials, int grid, double* out,

@@ -733,6 +733,17 @@ def test_adjoint_nonsymmetric():
     bnd.irk_apply_mass(ctx, uN - dev(d), g)
     bnd.irk_adjoint_run(ctx, ck, nsteps, every, g, None)
     assert np.linalg.norm(host(g) - lam) <= 1e-8 * np.linalg.norm(lam)
+    # the same instance through a batch graph (forward and adjoint launches)
+    u0d = dev(u0)
+    uNb = torch.empty_like(uN)
+    ckb = torch.empty_like(ck)
+    lamb = torch.empty_like(uN)
+    batch = bnd.irk_batch_create([ctx], nsteps, every, [u0d], [uNb], [ckb], [lamb], [None])
+    bnd.irk_batch_run(batch)
+    bnd.irk_apply_mass(ctx, uNb - dev(d), lamb)
+    bnd.irk_batch_adjoint(batch)
+    assert np.linalg.norm(host(lamb) - lam) <= 1e-8 * np.linalg.norm(lam)
+    batch.close()
     ctx.close()
 
 
