@@ -293,8 +293,10 @@ irk_status irk_run(irk_ctx* ctx, const double* d_u0, int32_t nsteps, double* d_u
  * is not NULL, adds dL/dkappa_e = -sum_i mu_i[e]^T K_e U_i[e] with the stage
  * values U_i = u_n + h_t sum_j a_ij k_j (heat problems with a mesh; F must be
  * sum_e kappa_e K_e).  d_u_n (n) and d_k_n (s*n) are the forward step's input
- * and stages.  d_lambda_n may alias d_lambda_np1.  IRK_ERR_INVALID if M or F
- * is not symmetric (the transposed hierarchies are not built). */
+ * and stages.  d_lambda_n may alias d_lambda_np1.  For nonsymmetric M or F the
+ * first adjoint call builds M^T, F^T and the AMG hierarchies of the transposed
+ * diagonal blocks (kept by the context).  The transposed system is solved with
+ * right-preconditioned FGMRES whatever the side of the forward solves. */
 irk_status irk_adjoint_step(irk_ctx* ctx, const double* d_lambda_np1, const double* d_u_n,
                             const double* d_k_n, double* d_lambda_n, double* d_grad_kappa,
                             irk_stats* stats);
@@ -342,7 +344,8 @@ void irk_batch_destroy(irk_batch* b);
  * ------------------------------------------------------------------------- */
 
 /* d_w = (I (x) M + h_t A (x) F) d_z; transpose != 0 applies
- * I (x) M^T + h_t A^T (x) F^T (symmetric M, F).  s*n each. */
+ * I (x) M^T + h_t A^T (x) F^T (for nonsymmetric M or F with the transposed
+ * matrices, built on first use).  s*n each. */
 irk_status irk_apply_operator(irk_ctx* ctx, const double* d_z, double* d_w, int32_t transpose);
 
 /* The same operator on an FP32 d_z (s*n floats), as FGMRES applies it to the

@@ -349,7 +349,8 @@ static irk_status adjoint_one(Ctx& c, const double* lam_in, const double* u_n, c
 }
 
 static void check_adjoint_ok(Ctx& c, bool need_grad) {
-  if (c.side != 0) fail(IRK_ERR_INVALID, "the adjoint runs right-preconditioned contexts only (side = 0)");
+  // the transposed stage systems are solved with right-preconditioned FGMRES for
+  // either side of the forward solve (the adjoint needs their solutions only)
   if (need_grad && c.n_tri == 0) fail(IRK_ERR_INVALID, "kappa gradient needs the mesh in irk_setup");
 }
 
@@ -801,6 +802,7 @@ irk_status irk_apply_operator(irk_ctx* h, const double* d_z, double* d_w, int32_
   if (!h || !d_z || !d_w) return set_err(h, IRK_ERR_INVALID, "NULL argument");
   return guarded(h, [&] {
     Ctx& c = h->c;
+    irk::AdjointView av(c, transpose != 0);
     irk::begin_call(c);
     irk::kron_apply_plain(c, d_z, d_w, transpose != 0, c.stream);
     c.launches += 1;
@@ -812,6 +814,7 @@ irk_status irk_apply_operator_f32(irk_ctx* h, const float* d_z, double* d_w, int
   if (!h || !d_z || !d_w) return set_err(h, IRK_ERR_INVALID, "NULL argument");
   return guarded(h, [&] {
     Ctx& c = h->c;
+    irk::AdjointView av(c, transpose != 0);
     irk::begin_call(c);
     irk::kron_apply_f32(c, d_z, d_w, transpose != 0, c.stream);
     c.launches += 1;

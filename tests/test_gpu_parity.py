@@ -713,6 +713,11 @@ def test_adjoint_nonsymmetric():
     ref = pc.apply(v)
     assert np.linalg.norm(host(z).reshape(3, -1) - ref) <= 1e-12 * np.linalg.norm(ref)
     sol = oirk.IRKSolver(prob, A, b, h, kind="LD", subsolve="direct")
+    zt = synth.random_stage_block(prob.n, 3, 12)
+    wt = torch.empty(3 * prob.n, dtype=torch.float64, device="cuda")
+    bnd.irk_apply_operator(ctx, dev(zt.ravel()), wt, transpose=True)
+    reft = sol.opT(zt)
+    assert np.abs(host(wt).reshape(3, -1) - reft).max() <= 1e-14 * np.abs(reft).max()
     lam1 = synth.random_smooth_u0(mesh, seed=5)
     ref_lam, _ = sol.adjoint_step(lam1, direct=True)
     out = torch.empty(prob.n, dtype=torch.float64, device="cuda")
@@ -744,6 +749,23 @@ def test_adjoint_nonsymmetric():
     bnd.irk_batch_adjoint(batch)
     assert np.linalg.norm(host(lamb) - lam) <= 1e-8 * np.linalg.norm(lam)
     batch.close()
+    ctx.close()
+
+
+def test_adjoint_of_left_preconditioned_context():
+    """A context whose forward solves are left-preconditioned runs its adjoint
+    steps with right-preconditioned FGMRES on the transposed system: one
+    adjoint step against the oracle's exact transposed solve."""
+    mesh, prob = heat(20)
+    A, b, _ = obt.radau_iia(3)
+    h = 0.05
+    ctx, _ = oracle_ctx(prob, A, "LD", h, amg_prec="f64", b=b, side="left", **AMG_OPTS)
+    sol = oirk.IRKSolver(prob, A, b, h, kind="LD", subsolve="direct")
+    lam1 = synth.random_smooth_u0(mesh, seed=8)
+    ref, _ = sol.adjoint_step(lam1, direct=True)
+    out = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    B().irk_adjoint_step(ctx, dev(lam1), None, None, out)
+    assert np.linalg.norm(host(out) - ref) <= 1e-8 * np.linalg.norm(ref)
     ctx.close()
 
 
