@@ -486,6 +486,7 @@ def run_sweep(args):
     """Configuration sweeps, one JSON line per run (right-preconditioned
     FGMRES(30), FP32 AMG unless stated; `--sweep-steps` timed steps after one
     untimed step, times per step from CUDA events):
+      c1  heat N = 32, Radau IIA s = 2, h_t = 0.05, J / GSL / GSL_OPT / DU / LD
       c2  heat N in {256, 512, 1024}, Radau IIA s in {3, 5, 7}, h_t = 1/64, J / GSL / GSL_OPT / DU / LD
       c3  double glazing N in {256, 512, 1024}, s = 2..7, h_t = 0.01, GSL / LD (one
           prolongator smoothing step: a second costs time without saving iterations here)
@@ -536,7 +537,13 @@ def run_sweep(args):
                           "amg_rows": rows}), flush=True)
         ctx.close()
 
-    if args.sweep == "c2":
+    if args.sweep == "c1":
+        # heat 32^2, Radau IIA s = 2, h_t = 0.05 (run with --sweep-steps 20, C1's count)
+        p = problems.heat(32)
+        u0 = synth.heat_u0(p["mesh"])
+        for kind in ("J", "GSL", "GSL_OPT", "DU", "LD"):
+            run(p, 2, 0.05, kind, u0, tag="c1")
+    elif args.sweep == "c2":
         for N in (256, 512, 1024):
             p = problems.heat(N)
             u0 = synth.heat_u0(p["mesh"])
@@ -844,7 +851,7 @@ def main():
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--strength", type=int, default=0, choices=[0, 1],
                     help="AMG strength measure for the P2 sweeps (t5 t6 t8): 0 |a_ij|, 1 max(-a_ij, 0)")
-    ap.add_argument("--sweep", default=None, choices=["c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t9", "t12", "t13"],
+    ap.add_argument("--sweep", default=None, choices=["c1", "c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t9", "t12", "t13"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--launch-list", action="store_true",
