@@ -660,7 +660,8 @@ def run_sweep(args):
                     h = (1.0 / hinv) ** (2.0 / (2 * s - 1))
                     kstar = torch.tensor(synth.random_stage_block(p["n"], s, 2000 + hinv).ravel(), device="cuda")
                     for kind in ("GSL", "LD"):
-                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", **SUPG_AMG)
+                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64",
+                                                  **dict(SUPG_AMG, cheb_degree=args.supg_degree))
                         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o,
                                           g=p["g"], stab=p["valT"])
                         rhs = torch.empty_like(kstar)
@@ -687,7 +688,8 @@ def run_sweep(args):
                 kstar = torch.tensor(synth.random_stage_block(p["n"], s, 3000 + s).ravel(), device="cuda")
                 for h in (0.05, 0.1, 0.5, 1.0, 5.0):
                     for kind in ("GSL", "LD"):
-                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64", **SUPG_AMG)
+                        o = B.irk_default_options(kind=kind, rtol=1e-8, side="left", amg_prec="f64",
+                                                  **dict(SUPG_AMG, cheb_degree=args.supg_degree))
                         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o,
                                           g=p["g"], stab=p["valT"])
                         rhs = torch.empty_like(kstar)
@@ -854,6 +856,8 @@ def main():
     ap.add_argument("--sweep", default=None, choices=["c1", "c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t9", "t12", "t13"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
+    ap.add_argument("--supg-degree", type=int, default=SUPG_AMG["cheb_degree"],
+                    help="Chebyshev degree of the SUPG sweeps (t12, t13)")
     ap.add_argument("--launch-list", action="store_true",
                     help="only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()
