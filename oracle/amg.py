@@ -50,6 +50,14 @@ reading fixed in the design notes, step by step:
                x_{k+1} = x_k + d_k.
              V(nu1, nu2) cycle from a zero initial guess (each sweep is one
              l1-Jacobi step or one Chebyshev polynomial of degree k).
+  cycle      "V" (the paper's one V-cycle per subsolve, default) or "Wc": the
+             finest level is visited once as in the V-cycle, and every coarser
+             level l >= 1 whose next level is not the coarsest applies the
+             coarse-grid correction twice (residual, restriction, recursion,
+             prolongation, then the same again) between its pre- and
+             post-smoothing, i.e. a W-cycle below the finest level.  A level
+             whose next level is the coarsest corrects once (with the exact
+             coarsest solve a second correction would be zero).
 """
 from __future__ import annotations
 
@@ -213,7 +221,11 @@ class Hierarchy:
 
     def __init__(self, A, theta=0.08, coarse_max=2048, max_levels=12,
                  nu_pre=1, nu_post=1, smoother="chebyshev", cheb_degree=4,
-                 cheb_lo=0.1, p_smooth=2, strength_negative=False, stab=None):
+                 cheb_lo=0.1, p_smooth=2, strength_negative=False, stab=None,
+                 cycle="V"):
+        if cycle not in ("V", "Wc"):
+            raise ValueError(cycle)
+        self.cycle = cycle
         self.theta = theta
         self.nu_pre = nu_pre
         self.nu_post = nu_post
@@ -291,9 +303,13 @@ class Hierarchy:
         x = np.zeros_like(b)
         for _ in range(self.nu_pre):
             x = self.smooth(lev, b, x)
-        r = b - lev.A @ x
-        e = self.vcycle(lev.R @ r, l + 1)
-        x = x + lev.P @ e
+        corrections = 1
+        if self.cycle == "Wc" and l >= 1 and l + 2 < len(self.levels):
+            corrections = 2
+        for _ in range(corrections):
+            r = b - lev.A @ x
+            e = self.vcycle(lev.R @ r, l + 1)
+            x = x + lev.P @ e
         for _ in range(self.nu_post):
             x = self.smooth(lev, b, x)
         return x
