@@ -491,6 +491,9 @@ def run_sweep(args):
       c3  double glazing N in {256, 512, 1024}, s = 2..7, h_t = 0.01, GSL / LD (one
           prolongator smoothing step: a second costs time without saving iterations here)
       c4  N = 1024, s = 5, LD: AMG in FP64 / FP32 / BF16-finest, heat and double glazing
+      mesh heat N in {256, 512, 1024}, s in {3, 5, 7}, h_t = h_x^(2/(2s-1)) (the time step
+          tied to the mesh as in the paper, P1), J / GSL / DU / LD, V-cycle and the W-cycle
+          below the finest level; then N = 1024, s = 5, h_t = 1/64, LD with both cycles
       ht  heat N = 128, s in {2, 7}, h_t in {0.05, 0.1, 0.5, 1, 5}, GSL / LD, rtol 1e-8
       lob heat N in {256, 1024}, Lobatto IIIC s in {2, 3, 4, 5}, h_t = 1/64, J / GSL / DU / LD
       htlr  as ht with FP64 AMG, left- and right-preconditioned (stop on the preconditioned /
@@ -515,9 +518,10 @@ def run_sweep(args):
     from paper_2010_11377_gb300 import problems
     steps = args.sweep_steps
 
-    def run(p, s, h, kind, u0, prec="f32", rtol=1e-10, tag="", method="radau_iia", side="right", p_smooth=2):
+    def run(p, s, h, kind, u0, prec="f32", rtol=1e-10, tag="", method="radau_iia", side="right", p_smooth=2,
+            cycle="V"):
         A, b, c = B.irk_butcher_table(method, s)
-        o = B.irk_default_options(kind=kind, amg_prec=prec, rtol=rtol, side=side, p_smooth=p_smooth)
+        o = B.irk_default_options(kind=kind, amg_prec=prec, rtol=rtol, side=side, p_smooth=p_smooth, cycle=cycle)
         t0 = time.perf_counter()
         ctx = B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h, options=o, g=p["g"])
         setup = time.perf_counter() - t0
@@ -530,7 +534,7 @@ def run_sweep(args):
         ms = st["ms"] / steps
         print(json.dumps({"sweep": tag, "problem": p["kind"], "method": method, "side": side, "N": p["N"], "n": p["n"],
                           "s": s, "h_t": h,
-                          "precond": kind, "amg": prec, "p_smooth": p_smooth, "rtol": rtol,
+                          "precond": kind, "amg": prec, "p_smooth": p_smooth, "cycle": cycle, "rtol": rtol,
                           "its_per_step": st["iterations"] / steps,
                           "max_step_its": st["max_step_iterations"], "ms_per_step": round(ms, 3),
                           "value": s * p["n"] / (ms * 1e-3), "resid": st["resid"], "setup_s": round(setup, 3),
@@ -557,6 +561,20 @@ def run_sweep(args):
             for s in (2, 3, 4, 5, 6, 7):
                 for kind in ("GSL", "LD"):
                     run(p, s, 0.01, kind, u0, tag="c3", p_smooth=1)
+    elif args.sweep == "mesh":
+        # h_x-independence with the time step tied to the mesh (h_t = h_x^(2/(2s-1)), P1),
+        # V-cycle and the W-cycle below the finest level; then the fixed-h_t C2 case at 1024^2
+        for N in (256, 512, 1024):
+            p = problems.heat(N)
+            u0 = synth.heat_u0(p["mesh"])
+            for s in (3, 5, 7):
+                for kind in ("J", "GSL", "DU", "LD"):
+                    for cyc in ("V", "Wc"):
+                        run(p, s, (1.0 / N) ** (2.0 / (2 * s - 1)), kind, u0, tag="mesh", cycle=cyc)
+        p = problems.heat(1024)
+        u0 = synth.heat_u0(p["mesh"])
+        for cyc in ("V", "Wc"):
+            run(p, 5, 1.0 / 64, "LD", u0, tag="mesh-c2", cycle=cyc)
     elif args.sweep == "c4":
         p = problems.heat(1024)
         u0 = synth.heat_u0(p["mesh"])
@@ -853,7 +871,7 @@ def main():
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--strength", type=int, default=0, choices=[0, 1],
                     help="AMG strength measure for the P2 sweeps (t5 t6 t8): 0 |a_ij|, 1 max(-a_ij, 0)")
-    ap.add_argument("--sweep", default=None, choices=["c1", "c2", "c3", "c4", "ht", "lob", "htlr", "t5", "t6", "t8", "t9", "t12", "t13"],
+    ap.add_argument("--sweep", default=None, choices=["c1", "c2", "c3", "c4", "mesh", "ht", "lob", "htlr", "t5", "t6", "t8", "t9", "t12", "t13"],
                     help="configuration sweep (one JSON line per run)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--supg-degree", type=int, default=SUPG_AMG["cheb_degree"],

@@ -66,6 +66,10 @@ enum {
 enum { IRK_AMG_F64 = 64, IRK_AMG_F32 = 32, IRK_AMG_BF16 = 16 /* BF16 finest matrix, FP32 elsewhere */ };
 
 enum { IRK_SMOOTH_L1JACOBI = 0, IRK_SMOOTH_CHEBYSHEV = 1 };
+/* AMG cycle of one subsolve: the V-cycle (Section 4.2), or the same finest-level
+ * visit with a W-cycle below it (every level l >= 1 whose next level is not the
+ * coarsest corrects twice) */
+enum { IRK_CYCLE_V = 0, IRK_CYCLE_W_COARSE = 1 };
 
 enum { IRK_METHOD_RADAU_IIA = 0, IRK_METHOD_LOBATTO_IIIC = 1 };
 
@@ -119,6 +123,15 @@ typedef struct {
                             the negative-only measure helps P2 heat blocks but can leave a
                             convection-dominated block without strong couplings (no
                             coarsening) */
+  int32_t cycle;         /* IRK_CYCLE_V (default): one V(nu_pre, nu_post) cycle per subsolve.
+                            IRK_CYCLE_W_COARSE: the finest level is visited once, as in the
+                            V-cycle; every coarser level l >= 1 whose next level is not the
+                            coarsest applies the coarse-grid correction (residual,
+                            restriction, recursion, prolongation) twice between its pre- and
+                            post-smoothing.  It keeps the subsolve's contraction at the
+                            two-grid rate on stiffness-dominated blocks (large h_t / h_x^2),
+                            where the V-cycle's rate degrades with the number of levels; it
+                            costs one more pass over levels 2.. per subsolve */
 } irk_options;
 
 typedef struct {
@@ -157,7 +170,7 @@ irk_status irk_atilde(int32_t kind, int32_t s, const double* A, double* Atilde, 
 /* Fill *opt with the defaults: P_LD, FP32 AMG, Chebyshev degree 4 on [0.1, 1],
  * V(1,1), theta 0.08, coarse_max 2048, 12 levels, FGMRES(30), rtol 1e-10,
  * max_it 1000, selective reorthogonalisation (reorth_eta 0.1), right preconditioning,
- * two prolongator smoothing steps, strength from |a_ij|. */
+ * two prolongator smoothing steps, strength from |a_ij|, the V-cycle. */
 void irk_default_options(irk_options* opt);
 
 /* ------------------------------------------------------------------------- *

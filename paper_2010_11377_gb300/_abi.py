@@ -28,7 +28,7 @@ class IrkOptions(C.Structure):
                 ("coarse_max", C.c_int32), ("max_levels", C.c_int32), ("restart", C.c_int32),
                 ("rtol", C.c_double), ("max_it", C.c_int32), ("reorth", C.c_int32),
                 ("reorth_eta", C.c_double), ("side", C.c_int32), ("p_smooth", C.c_int32),
-                ("strength", C.c_int32)]
+                ("strength", C.c_int32), ("cycle", C.c_int32)]
 
 
 class IrkStats(C.Structure):

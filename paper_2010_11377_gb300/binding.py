@@ -15,6 +15,7 @@ PC_KINDS = {"J": 0, "GSL": 1, "GSL_OPT": 2, "DU": 3, "LD": 4, "CUSTOM": 5}
 METHODS = {"radau_iia": 0, "lobatto_iiic": 1}
 AMG_PREC = {"f64": 64, "f32": 32, "bf16": 16, 64: 64, 32: 32, 16: 16}
 SMOOTHERS = {"l1jacobi": 0, "chebyshev": 1}
+CYCLES = {"V": 0, "Wc": 1}
 
 
 def _dp(a):
@@ -81,6 +82,8 @@ def irk_default_options(**overrides) -> IrkOptions:
             v = {"right": 0, "left": 1}[v] if isinstance(v, str) else v
         elif k == "smoother":
             v = SMOOTHERS[v] if isinstance(v, str) else v
+        elif k == "cycle":
+            v = CYCLES[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 

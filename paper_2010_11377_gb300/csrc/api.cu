@@ -448,6 +448,7 @@ void irk_default_options(irk_options* o) {
   o->side = 0;
   o->p_smooth = 2;
   o->strength = 0;
+  o->cycle = IRK_CYCLE_V;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -497,6 +498,8 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
   if (o.side != 0 && o.side != 1) return set_err(nullptr, IRK_ERR_INVALID, "side must be 0 (right) or 1 (left)");
   if (o.p_smooth < 1 || o.p_smooth > 3) return set_err(nullptr, IRK_ERR_INVALID, "p_smooth must be 1, 2 or 3");
   if (o.strength != 0 && o.strength != 1) return set_err(nullptr, IRK_ERR_INVALID, "strength must be 0 or 1");
+  if (o.cycle != IRK_CYCLE_V && o.cycle != IRK_CYCLE_W_COARSE)
+    return set_err(nullptr, IRK_ERR_INVALID, "cycle must be IRK_CYCLE_V or IRK_CYCLE_W_COARSE");
   if (o.coarse_max < 1 || o.coarse_max > irk::MAX_COARSE)
     return set_err(nullptr, IRK_ERR_INVALID, "coarse_max must be 1..2048");
   const irk_csr& M = prob->M;
@@ -548,6 +551,7 @@ irk_status irk_setup(const irk_problem* prob, const irk_butcher* bt, double h_t,
     c.amg.cheb_lo = o.cheb_lo;
     c.amg.p_smooth = o.p_smooth;
     c.amg.strength_negative = o.strength;
+    c.amg.w_coarse = o.cycle == IRK_CYCLE_W_COARSE ? 1 : 0;
     c.amg.nu_pre = o.nu_pre;
     c.amg.nu_post = o.nu_post;
     c.amg.amg_prec = o.amg_prec;

@@ -243,6 +243,7 @@ struct AmgParams {
   int amg_prec = 32;
   int p_smooth = 2;        // damped-Jacobi steps on the tentative prolongator
   int strength_negative = 0;   // strength from max(-a_ij, 0) (else |a_ij|)
+  int w_coarse = 0;        // W-cycle below the finest level (two coarse-grid corrections on levels >= 1)
 };
 
 // Chebyshev step coefficients: step i updates d_i = alpha_i d_{i-1} + beta_i D^{-1}(b - A x_i)

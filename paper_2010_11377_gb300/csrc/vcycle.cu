@@ -384,45 +384,53 @@ struct VCycle {
         }
       }
     }
-    // ---- residual and restriction
+    // ---- coarse-grid correction(s): once in the V-cycle; twice on levels l >= 1 of the
+    // W-cycle below the finest level, unless the next level is the coarsest
     const T beta0 = T(sc.beta[0]);
-    if (p.nu_pre > 0) {
-      LMat<V> A = lmat<V>(L.Am);
-      const T* dv = static_cast<const T*>(L.dinv);
-      IRK_DISPATCH_L(L.Am.lanes, {
-        if (implicit)
-          launch_k(k_resid<V, T, LN, XM_IMPLICIT>, grid_for(L.Am), 256, 0, st, A, dv, b, nullptr, beta0, rb);
-        else
-          launch_k(k_resid<V, T, LN, XM_EXPLICIT>, grid_for(L.Am), 256, 0, st, A, dv, b, cur, beta0, rb);
-      });
-      ++launches;
-      count_matvec<V>(L, 2, 1);
-    }
+    const int corrections = (p.w_coarse && l >= 1 && l + 2 <= last) ? 2 : 1;
     const Level& C = H.lv[l + 1];
-    {
-      LMat<T> R = lmat<T>(L.Rm);
-      const T* src = p.nu_pre > 0 ? rb : b;
-      IRK_DISPATCH_L(L.Rm.lanes, { launch_k(k_spmv<T, LN>, grid_for(L.Rm), 256, 0, st, R, src, static_cast<T*>(C.b)); });
+    for (int corr = 0; corr < corrections; ++corr) {
+      const bool first = corr == 0;
+      const bool have_x = p.nu_pre > 0 || !first;   // else x = 0 and the residual is b
+      // residual r = b - A x (x implicit after a first step from zero)
+      if (have_x) {
+        LMat<V> A = lmat<V>(L.Am);
+        const T* dv = static_cast<const T*>(L.dinv);
+        IRK_DISPATCH_L(L.Am.lanes, {
+          if (first && implicit)
+            launch_k(k_resid<V, T, LN, XM_IMPLICIT>, grid_for(L.Am), 256, 0, st, A, dv, b, nullptr, beta0, rb);
+          else
+            launch_k(k_resid<V, T, LN, XM_EXPLICIT>, grid_for(L.Am), 256, 0, st, A, dv, b, cur, beta0, rb);
+        });
+        ++launches;
+        count_matvec<V>(L, 2, 1);
+      }
+      // restriction
+      {
+        LMat<T> R = lmat<T>(L.Rm);
+        const T* src = have_x ? rb : b;
+        IRK_DISPATCH_L(L.Rm.lanes, { launch_k(k_spmv<T, LN>, grid_for(L.Rm), 256, 0, st, R, src, static_cast<T*>(C.b)); });
+      }
+      ++launches;
+      cost.bytes += double(L.Rm.nnz) * (sizeof(int) + sizeof(T)) + double(L.n + C.n) * sizeof(T);
+      cost.flops += 2.0 * double(L.Rm.nnz);
+      T* e = level<T>(l + 1, none);
+      // prolongation and correction x += P e (x = beta0 D^-1 b + P e after an implicit step)
+      {
+        LMat<T> P = lmat<T>(L.Pm);
+        const T* dv = static_cast<const T*>(L.dinv);
+        if (!have_x) CK(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, st));
+        IRK_DISPATCH_L(L.Pm.lanes, {
+          if (first && p.nu_pre > 0 && implicit)
+            launch_k(k_prolong<T, LN, true>, grid_for(L.Pm), 256, 0, st, P, e, cur, dv, b, beta0);
+          else
+            launch_k(k_prolong<T, LN, false>, grid_for(L.Pm), 256, 0, st, P, e, cur, nullptr, nullptr, beta0);
+        });
+      }
+      ++launches;
+      cost.bytes += double(L.Pm.nnz) * (sizeof(int) + sizeof(T)) + double(2 * L.n + C.n) * sizeof(T);
+      cost.flops += 2.0 * double(L.Pm.nnz);
     }
-    ++launches;
-    cost.bytes += double(L.Rm.nnz) * (sizeof(int) + sizeof(T)) + double(L.n + C.n) * sizeof(T);
-    cost.flops += 2.0 * double(L.Rm.nnz);
-    T* e = level<T>(l + 1, none);
-    // ---- prolongation and correction
-    {
-      LMat<T> P = lmat<T>(L.Pm);
-      const T* dv = static_cast<const T*>(L.dinv);
-      if (p.nu_pre == 0) CK(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, st));
-      IRK_DISPATCH_L(L.Pm.lanes, {
-        if (p.nu_pre > 0 && implicit)
-          launch_k(k_prolong<T, LN, true>, grid_for(L.Pm), 256, 0, st, P, e, cur, dv, b, beta0);
-        else
-          launch_k(k_prolong<T, LN, false>, grid_for(L.Pm), 256, 0, st, P, e, cur, nullptr, nullptr, beta0);
-      });
-    }
-    ++launches;
-    cost.bytes += double(L.Pm.nnz) * (sizeof(int) + sizeof(T)) + double(2 * L.n + C.n) * sizeof(T);
-    cost.flops += 2.0 * double(L.Pm.nnz);
     // ---- post-smoothing
     int total = p.nu_post * steps;
     int q = 0;

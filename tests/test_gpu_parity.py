@@ -223,6 +223,43 @@ def test_vcycle_parity(prec, tol):
             assert np.linalg.norm(host(x) - exact_ref) < 0.1 * np.linalg.norm(exact_ref)
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_coarse_w_cycle_parity(prec, tol):
+    """The W-cycle below the finest level (IRK_CYCLE_W_COARSE) against the
+    oracle's on hierarchies of four or more levels (stiffness-dominated heat
+    blocks, h_t = 4, 97^2 with a ragged tail, coarsest at most 16 rows): one
+    cycle per stage through irk_vcycle, and the LD preconditioner (both
+    directions) through irk_apply_precond."""
+    mesh, prob = heat(97)
+    A, _, _ = obt.radau_iia(2)
+    h = 4.0
+    opts = dict(AMG_OPTS, coarse_max=16)
+    oopts = dict(oracle_amg_opts(), coarse_max=16)
+    ctx, At = oracle_ctx(prob, A, "LD", h, amg_prec=prec, cycle="Wc", **opts)
+    rhs = synth.random_stage_block(prob.n, 1, 21)[0]
+    for stage in range(2):
+        Bk = (prob.M + (h * At[stage, stage]) * prob.F).tocsr()
+        H = oamg.Hierarchy(Bk, cycle="Wc", **oopts)
+        assert len(H.sizes()) >= 4, H.sizes()
+        ref = H.vcycle(rhs)
+        x = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        B().irk_vcycle(ctx, stage, dev(rhs), x)
+        err = np.linalg.norm(host(x) - ref) / np.linalg.norm(ref)
+        assert err < tol, (prec, stage, err)
+        vref = oamg.Hierarchy(Bk, **oopts).vcycle(rhs)
+        assert np.linalg.norm(vref - ref) > 100 * tol * np.linalg.norm(ref)
+    v = synth.random_stage_block(prob.n, 2, 22)
+    for tr in (False, True):
+        pc = oirk.BlockPreconditioner(prob.M, prob.F, A, h, "LD", "amg", Atilde=At,
+                                      amg_opts=dict(oopts, cycle="Wc"), transpose=tr)
+        ref = pc.apply(v)
+        z = torch.empty(2 * prob.n, dtype=torch.float64, device="cuda")
+        B().irk_apply_precond(ctx, dev(v.ravel()), z, transpose=tr)
+        err = np.linalg.norm(host(z).reshape(2, -1) - ref) / np.linalg.norm(ref)
+        assert err < 2 * tol, (prec, tr, err)
+    ctx.close()
+
+
 @pytest.mark.parametrize("kind", ["J", "GSL", "GSL_OPT", "DU", "LD"])
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
 def test_precond_parity(kind, prec, tol):
