@@ -31,6 +31,35 @@ def kron_matrix(M, F, A, h):
     return (sp.kron(sp.identity(s), M) + h * sp.kron(sp.csr_matrix(A), F)).tocsc()
 
 
+def solve_stages_eig(M, F, A, h, rhs):
+    """Exact solve of (I_s (x) M + h A (x) F) k = rhs for a diagonalisable
+    Butcher matrix (the Radau IIA tables have distinct eigenvalues), by the
+    eigendecomposition A = S diag(lam) S^-1: multiplying by S^-1 (x) I
+    decouples the stages into the s sparse systems
+        (M + h lam_j F) y_j = sum_i (S^-1)_ji rhs_i,   k = (S (x) I) y.
+    A real A has eigenvalues in conjugate pairs whose solutions are conjugate,
+    so each pair takes one complex sparse LU.  For sizes where the assembled
+    sN x sN system is too large for a direct solve."""
+    s = A.shape[0]
+    lam, S = np.linalg.eig(A)
+    R = np.linalg.solve(S, rhs.astype(complex))
+    Y = np.zeros((s, rhs.shape[1]), dtype=complex)
+    done = [False] * s
+    for j in range(s):
+        if done[j]:
+            continue
+        Bj = (M + (h * lam[j]) * F).tocsc()
+        Y[j] = spla.splu(Bj).solve(R[j])
+        done[j] = True
+        if abs(lam[j].imag) > 0.0:
+            for q in range(s):
+                if not done[q] and abs(lam[q] - np.conj(lam[j])) <= 1e-12 * abs(lam[j]):
+                    Y[q] = np.conj(Y[j])     # real A, real rhs: R_q = conj(R_j)
+                    done[q] = True
+                    break
+    return np.real(S @ Y)
+
+
 def stage_rhs(F, g, u, s):
     """Right-hand side -(1_s (x) (F u_n + g)) of Eq. block_coeff_mtx
     (g = F_IB u_B is the Dirichlet lift, zero for the heat problem)."""

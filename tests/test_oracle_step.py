@@ -88,6 +88,30 @@ def test_operator_matches_kron():
     assert np.allclose(w1, w2, atol=1e-14, rtol=0)
 
 
+@pytest.mark.parametrize("s", [1, 2, 3, 5, 7])
+def test_eigen_decoupled_solve_equals_the_kronecker_lu(s):
+    """The stage solve through the eigendecomposition of A (s decoupled sparse
+    systems, one complex LU per conjugate pair) equals the LU solve of the
+    assembled Kronecker system, for Radau IIA tables with a real eigenvalue
+    and with conjugate pairs, on a stage right-hand side and a random one."""
+    mesh, prob = _heat(23)
+    A, _, _ = bt.radau_iia(s)
+    h = 0.05
+    K = irk.kron_matrix(prob.M, prob.F, A, h)
+    for rhs in (irk.stage_rhs(prob.F, prob.g, synth.heat_u0(mesh), s),
+                synth.random_stage_block(prob.n, s, 31)):
+        ref = sla_spsolve(K, rhs)
+        got = irk.solve_stages_eig(prob.M, prob.F, A, h, rhs)
+        assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref), s
+    lam = np.linalg.eigvals(A)
+    assert (s % 2 == 1) == bool(np.any(np.abs(lam.imag) < 1e-14))   # one real eigenvalue iff s odd
+
+
+def sla_spsolve(K, rhs):
+    import scipy.sparse.linalg as spla
+    return spla.spsolve(K, rhs.ravel()).reshape(rhs.shape)
+
+
 @pytest.mark.parametrize("kind", ["J", "GSL", "GSL_OPT", "DU", "LD"])
 def test_preconditioner_substitution_is_exact(kind):
     """Section 4.2: the substitution with exact subsolves equals a dense solve
