@@ -142,23 +142,27 @@ k_smooth(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T
   int r, lane;
   row_lane<L>(gid, r, lane);
   bool valid = r < A.n;
+  // the row's own vector entries are loaded first, so that they are in flight with the
+  // row product's chain (slice base -> offsets and values -> gathered x)
+  const bool owner = valid && lane == 0;
+  T dr = T(0), br = T(0), xr = T(0), dprev = T(0);
+  if (owner) {
+    dr = dinv[r];
+    br = b[r];
+    if (XM == XM_EXPLICIT) {
+      xr = xin[r];
+      if (din) dprev = din[r];
+    }
+  }
   T ax = T(0);
   if (XM != XM_ZERO)
     ax = row_dot<L, V, T>(A, valid ? r : -1, lane, [&](int c) {
       return (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : xin[c];
     });
-  if (!valid || lane != 0) return;
-  T dr = dinv[r], br = b[r];
-  T xr, dprev;
-  if (XM == XM_EXPLICIT) {
-    xr = xin[r];
-    dprev = din ? din[r] : T(0);
-  } else if (XM == XM_IMPLICIT) {
+  if (!owner) return;
+  if (XM == XM_IMPLICIT) {
     xr = beta0 * dr * br;
     dprev = xr;
-  } else {
-    xr = T(0);
-    dprev = T(0);
   }
   T res = dr * (br - ax);
   T d = alpha * dprev + beta * res;
@@ -179,10 +183,12 @@ k_resid(LMat<V> A, const T* __restrict__ dinv, const T* __restrict__ b, const T*
   int r, lane;
   row_lane<L>(gid, r, lane);
   bool valid = r < A.n;
+  const bool owner = valid && lane == 0;
+  const T br = owner ? b[r] : T(0);   // in flight with the row product
   T ax = row_dot<L, V, T>(A, valid ? r : -1, lane, [&](int c) {
     return (XM == XM_IMPLICIT) ? beta0 * dinv[c] * b[c] : x[c];
   });
-  if (valid && lane == 0) r_out[r] = b[r] - ax;
+  if (owner) r_out[r] = br - ax;
 }
 
 // y = R x (restriction)
@@ -209,8 +215,11 @@ k_prolong(LMat<T> P, const T* __restrict__ e, T* x, const T* __restrict__ dinv, 
   int r, lane;
   row_lane<L>(gid, r, lane);
   bool valid = r < P.n;
+  const bool owner = valid && lane == 0;
+  T x0 = T(0);   // in flight with the row product
+  if (owner) x0 = IMPLICIT ? beta0 * dinv[r] * b[r] : x[r];
   T s = row_dot<L, T, T>(P, valid ? r : -1, lane, [&](int c) { return e[c]; });
-  if (valid && lane == 0) x[r] = (IMPLICIT ? beta0 * dinv[r] * b[r] : x[r]) + s;
+  if (owner) x[r] = x0 + s;
 }
 
 // coarsest level: x = A^{-1} b with the stored dense inverse; one warp per row
