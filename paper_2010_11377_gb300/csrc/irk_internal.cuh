@@ -108,6 +108,9 @@ struct CsrD {               // device CSR, FP64 values, int32 indices
   double* val = nullptr;
 };
 
+constexpr int PAT_W = 8;    // widest shared slice pattern (one 16-byte slot per slice)
+static_assert(PAT_W * sizeof(short) == 16, "one 16-byte slot per slice");
+
 struct Sell {               // SELL: slices of 32 / tpr rows, tpr threads per row (1: SELL-32)
   int n = 0, ncols = 0, nslices = 0;
   int tpr = 1;
@@ -119,10 +122,12 @@ struct Sell {               // SELL: slices of 32 / tpr rows, tpr threads per ro
   // the bandwidth-bound kernels instead of col (2 bytes per entry less)
   short* dcol = nullptr;
   // SELL-32 with 16-bit offsets: slices whose 32 rows all have the same length
-  // and the same offsets (the interior of a stencil in natural order) keep one
-  // offset per chunk, pdcol[sptr[sl] / 32 + k], read once per warp instead of
-  // 32 times; suni[sl] = 1 marks them.  nnz_nonuni counts the stored entries of
-  // the other slices (whose per-entry offsets are read).
+  // w <= PAT_W and the same offsets (the interior of a stencil in natural order)
+  // keep one offset per chunk in a fixed 16-byte slot of the slice,
+  // pdcol[PAT_W sl + k] (k < w, zero beyond), read once per warp instead of 32
+  // times and without waiting for the slice base; suni[sl] = w marks them
+  // (0: per-entry offsets).  nnz_nonuni counts the stored entries of the other
+  // slices (whose per-entry offsets are read).
   unsigned char* suni = nullptr;
   short* pdcol = nullptr;
   int64_t nnz_nonuni = 0;
@@ -138,8 +143,8 @@ struct SellView {
   const int* __restrict__ col;
   const V* __restrict__ val;
   const short* __restrict__ dcol;
-  const unsigned char* __restrict__ suni;   // uniform-pattern slices, or null
-  const short* __restrict__ pdcol;          // their per-chunk offsets
+  const unsigned char* __restrict__ suni;   // width of the slice's shared pattern (0: none), or null
+  const short* __restrict__ pdcol;          // the patterns, PAT_W offsets per slice
 };
 
 // column of SELL entry idx of row r
@@ -190,8 +195,8 @@ struct LMat {
   const int* __restrict__ col;
   const V* __restrict__ val;
   const short* __restrict__ dcol;   // 16-bit column offsets from the row (SELL or CSR), or null
-  const unsigned char* __restrict__ suni;   // SELL-32: uniform-pattern slices, or null
-  const short* __restrict__ pdcol;
+  const unsigned char* __restrict__ suni;   // SELL-32: width of the slice's shared pattern (0: none), or null
+  const short* __restrict__ pdcol;          // the patterns, PAT_W offsets per slice
 };
 
 template <typename V>

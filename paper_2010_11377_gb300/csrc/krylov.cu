@@ -320,7 +320,7 @@ k_kron_ff(int n, SellView<double> Mv, const float4* __restrict__ mf, JPtr<const 
     int sl = r >> 5, lane = r & 31;
     int64_t base = Mv.sptr[sl];
     int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
-    const short* __restrict__ pd = (Mv.suni && Mv.suni[sl]) ? Mv.pdcol + (base >> 5) : nullptr;
+    const short* __restrict__ pd = (Mv.suni && Mv.suni[sl]) ? Mv.pdcol + int64_t(sl) * PAT_W : nullptr;
     for (int k = 0; k < wdt; ++k) {
       int64_t idx = base + (int64_t(k) << 5) + lane;
       int c = pd ? r + static_cast<int>(pd[k]) : sell_col(Mv.col, Mv.dcol, idx, r);

@@ -335,7 +335,8 @@ __global__ void k_sell_offsets(int n, int nslices, int tpr, const int* __restric
 }
 
 // one warp per SELL-32 slice: the slice shares one offset pattern when its 32
-// rows are all real, all as long as the slice is wide, and agree chunk by chunk
+// rows are all real, all as long as the slice is wide (at most PAT_W), and agree
+// chunk by chunk; the pattern goes to the slice's slot pdcol[PAT_W sl ..]
 __global__ void k_sell_uniform(int n, int nslices, const int* __restrict__ rowptr, const int64_t* __restrict__ sptr,
                                const short* __restrict__ dcol, unsigned char* __restrict__ suni,
                                short* __restrict__ pdcol, unsigned long long* __restrict__ nonuni) {
@@ -351,13 +352,13 @@ __global__ void k_sell_uniform(int n, int nslices, const int* __restrict__ rowpt
     short d0 = __shfl_sync(0xffffffffu, d, 0);
     ok = ok && d == d0;
   }
-  bool all = __all_sync(0xffffffffu, ok);
+  bool all = __all_sync(0xffffffffu, ok) && w >= 1 && w <= PAT_W;
   if (lane == 0) {
-    suni[sl] = all ? 1 : 0;
+    suni[sl] = all ? static_cast<unsigned char>(w) : 0;
     if (!all) atomicAdd(nonuni, static_cast<unsigned long long>(w) * SELL_C);
   }
-  if (all)
-    for (int k = lane; k < w; k += 32) pdcol[(base >> 5) + k] = dcol[base + (int64_t(k) << 5)];
+  if (lane < PAT_W)
+    pdcol[int64_t(sl) * PAT_W + lane] = (all && lane < w) ? dcol[base + (int64_t(lane) << 5)] : short(0);
 }
 
 // the same for CSR (one thread per row)
@@ -424,7 +425,7 @@ void csr_to_sell(const CsrD& A, Sell& S, int want64, int want32, int want16, Dev
   S.nnz_nonuni = S.nnz_pad;
   if (S.dcol && tpr == 1 && sell_offsets_enabled() && slice_patterns_enabled()) {
     S.suni = pool.get<unsigned char>(ns);
-    S.pdcol = pool.get<short>(np / SELL_C + 1);
+    S.pdcol = pool.get<short>(size_t(ns) * PAT_W);
     Tmp tmp;
     unsigned long long* nonuni = tmp.get<unsigned long long>(1);
     CK(cudaMemsetAsync(nonuni, 0, sizeof(unsigned long long), st));

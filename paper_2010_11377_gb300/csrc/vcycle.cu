@@ -72,16 +72,27 @@ __device__ __forceinline__ T row_dot(const LMat<V>& A, int r, int lane, XF xf) {
   if constexpr (L == 1) {
     if (r >= 0) {
       int sl = r >> 5, ln = r & 31;
+      int wu = 0;
+      union {
+        int4 v;
+        short o[PAT_W];
+      } pat;
+      if (A.suni) {
+        // the slice's shared pattern: its width and its 16-byte slot are loaded
+        // alongside the slice base, so the gathers of x do not wait for the base
+        wu = A.suni[sl];
+        pat.v = reinterpret_cast<const int4*>(A.pdcol)[sl];
+      }
       int64_t base = A.sptr[sl];
+      if (wu) {
+#pragma unroll
+        for (int k = 0; k < PAT_W; ++k)
+          if (k < wu)
+            acc = fma(widen(A.val[base + (int64_t(k) << 5) + ln]), xf(r + static_cast<int>(pat.o[k])), acc);
+        return acc;
+      }
       int w = static_cast<int>((A.sptr[sl + 1] - base) >> 5);
-      if (A.suni && A.suni[sl]) {
-        // the slice's shared pattern: one offset per chunk for the whole warp
-        const short* __restrict__ pd = A.pdcol + (base >> 5);
-        for (int k = 0; k < w; ++k) {
-          int64_t idx = base + (int64_t(k) << 5) + ln;
-          acc = fma(widen(A.val[idx]), xf(r + static_cast<int>(pd[k])), acc);
-        }
-      } else if (A.dcol) {
+      if (A.dcol) {
         for (int k = 0; k < w; ++k) {
           int64_t idx = base + (int64_t(k) << 5) + ln;
           acc = fma(widen(A.val[idx]), xf(r + static_cast<int>(A.dcol[idx])), acc);
@@ -575,7 +586,7 @@ k_sweep_rhs(SellView<T> F, const double* __restrict__ V, const int* __restrict__
   int sl = r >> 5, lane = r & 31;
   int64_t base = F.sptr[sl];
   int w = static_cast<int>((F.sptr[sl + 1] - base) >> 5);
-  const short* __restrict__ pd = (F.suni && F.suni[sl]) ? F.pdcol + (base >> 5) : nullptr;
+  const short* __restrict__ pd = (F.suni && F.suni[sl]) ? F.pdcol + int64_t(sl) * PAT_W : nullptr;
   for (int k = 0; k < w; ++k) {
     int64_t idx = base + (int64_t(k) << 5) + lane;
     int c = pd ? r + static_cast<int>(pd[k]) : sell_col(F.col, F.dcol, idx, r);
