@@ -317,19 +317,36 @@ k_kron_ff(int n, SellView<double> Mv, const float4* __restrict__ mf, JPtr<const 
       fh[i] = 0.f;
       fl[i] = 0.f;
     }
-    int sl = r >> 5, lane = r & 31;
-    int64_t base = Mv.sptr[sl];
-    int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
-    const short* __restrict__ pd = (Mv.suni && Mv.suni[sl]) ? Mv.pdcol + int64_t(sl) * PAT_W : nullptr;
-    for (int k = 0; k < wdt; ++k) {
-      int64_t idx = base + (int64_t(k) << 5) + lane;
-      int c = pd ? r + static_cast<int>(pd[k]) : sell_col(Mv.col, Mv.dcol, idx, r);
+    auto entry = [&](int64_t idx, int c) {
       const float4 q = mf[idx];
 #pragma unroll
       for (int i = 0; i < S; ++i) {
         const float zz = z[int64_t(i) * n + c];
         ff_fma1(mh[i], ml[i], q.x, q.y, zz);
         ff_fma1(fh[i], fl[i], q.z, q.w, zz);
+      }
+    };
+    int sl = r >> 5, lane = r & 31;
+    // a shared slice pattern (width and 16-byte slot) is loaded alongside the slice base
+    int wu = 0;
+    union {
+      int4 v;
+      short o[PAT_W];
+    } pat;
+    if (Mv.suni) {
+      wu = Mv.suni[sl];
+      pat.v = reinterpret_cast<const int4*>(Mv.pdcol)[sl];
+    }
+    int64_t base = Mv.sptr[sl];
+    if (wu) {
+#pragma unroll
+      for (int k = 0; k < PAT_W; ++k)
+        if (k < wu) entry(base + (int64_t(k) << 5) + lane, r + static_cast<int>(pat.o[k]));
+    } else {
+      int wdt = static_cast<int>((Mv.sptr[sl + 1] - base) >> 5);
+      for (int k = 0; k < wdt; ++k) {
+        int64_t idx = base + (int64_t(k) << 5) + lane;
+        entry(idx, sell_col(Mv.col, Mv.dcol, idx, r));
       }
     }
 #pragma unroll

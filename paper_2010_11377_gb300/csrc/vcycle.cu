@@ -583,16 +583,33 @@ k_sweep_rhs(SellView<T> F, const double* __restrict__ V, const int* __restrict__
   T acc[NP > 0 ? NP : 1];
 #pragma unroll
   for (int q = 0; q < NP; ++q) acc[q] = T(0);
-  int sl = r >> 5, lane = r & 31;
-  int64_t base = F.sptr[sl];
-  int w = static_cast<int>((F.sptr[sl + 1] - base) >> 5);
-  const short* __restrict__ pd = (F.suni && F.suni[sl]) ? F.pdcol + int64_t(sl) * PAT_W : nullptr;
-  for (int k = 0; k < w; ++k) {
-    int64_t idx = base + (int64_t(k) << 5) + lane;
-    int c = pd ? r + static_cast<int>(pd[k]) : sell_col(F.col, F.dcol, idx, r);
+  auto entry = [&](int64_t idx, int c) {
     T f = F.val[idx];
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc[q] = fma(f, zj[int64_t(cp.idx[q]) * n + c], acc[q]);
+  };
+  int sl = r >> 5, lane = r & 31;
+  // a shared slice pattern (width and 16-byte slot) is loaded alongside the slice base
+  int wu = 0;
+  union {
+    int4 v;
+    short o[PAT_W];
+  } pat;
+  if (F.suni) {
+    wu = F.suni[sl];
+    pat.v = reinterpret_cast<const int4*>(F.pdcol)[sl];
+  }
+  int64_t base = F.sptr[sl];
+  if (wu) {
+#pragma unroll
+    for (int k = 0; k < PAT_W; ++k)
+      if (k < wu) entry(base + (int64_t(k) << 5) + lane, r + static_cast<int>(pat.o[k]));
+  } else {
+    int w = static_cast<int>((F.sptr[sl + 1] - base) >> 5);
+    for (int k = 0; k < w; ++k) {
+      int64_t idx = base + (int64_t(k) << 5) + lane;
+      entry(idx, sell_col(F.col, F.dcol, idx, r));
+    }
   }
   T res = v;
 #pragma unroll
