@@ -412,3 +412,23 @@ def test_fgmres_arnoldi_relation():
     y, *_ = np.linalg.lstsq(H, np.eye(k + 1)[:, 0] * np.linalg.norm(rhs), rcond=None)
     r_true = np.linalg.norm(rhs.ravel() - AZ @ y)
     assert abs(r_true - rec["estimate"]) <= 1e-9 * np.linalg.norm(rhs)
+
+
+def test_counts_depend_on_the_time_step_to_mesh_ratio_not_on_the_mesh():
+    """h_x-independence (Section 5.1, Table 5) of FGMRES with P_LD and one AMG
+    V-cycle per subsolve (s = 5, rtol 1e-10): at a fixed ratio h_t / h_x^2
+    (the balance of mass and stiffness in the diagonal blocks) the counts at
+    64^2, 128^2 and 256^2 differ by at most 1, while at a fixed h_t the ratio
+    grows 16-fold over the same meshes and the count with it."""
+    A, b, _ = bt.radau_iia(5)
+
+    def its(N, h):
+        mesh = synth.structured_mesh(N)
+        prob = fem.heat_problem(mesh)
+        return irk.IRKSolver(prob, A, b, h, kind="LD", subsolve="amg").step(synth.heat_u0(mesh)).iterations
+
+    for ratio in (4096.0, 16384.0):
+        counts = [its(N, ratio / N ** 2) for N in (64, 128, 256)]
+        assert max(counts) - min(counts) <= 1, (ratio, counts)
+    fixed = [its(N, 1 / 64) for N in (64, 256)]
+    assert fixed[1] - fixed[0] >= 2, fixed
