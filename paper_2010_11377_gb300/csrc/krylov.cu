@@ -135,10 +135,15 @@ __device__ __forceinline__ bool last_block(GmresState* st) {
   return am;
 }
 
-// total of slot q over all blocks, in block order
-__device__ __forceinline__ double gather_partials(const double* partials, int q) {
+// Sum of partial q over the grid's blocks, by one whole warp (every lane returns it): the
+// lanes load strided partials, so the loads are in flight together, and meet in a shuffle
+// tree.  Deterministic: the order depends only on the grid size.
+__device__ __forceinline__ double warp_gather_partials(const double* partials, int q) {
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int b = 0; b < static_cast<int>(gridDim.x); ++b) s += ldcg(partials + int64_t(b) * PL + q);
+  for (int b = lane; b < static_cast<int>(gridDim.x); b += 32) s += ldcg(partials + int64_t(b) * PL + q);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
@@ -237,8 +242,10 @@ k_kron(int n, SellView<double> Mv, const double* __restrict__ Fval, JPtr<const T
     double v[1] = {nrm};
     block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
     if (last_block(st)) {
+      double b2 = 0.0;
+      if (threadIdx.x < 32) b2 = warp_gather_partials(partials, 0);
       if (threadIdx.x == 0) {
-        double beta = sqrt(gather_partials(partials, 0));
+        double beta = sqrt(b2);
         st->resid = beta / st->bnorm;
         st->cycle_end = 0;
         if (!isfinite(beta)) {
@@ -426,8 +433,10 @@ k_gs_dots(GmresState* st, const double* __restrict__ V, int64_t ldv, int64_t N, 
     i0 += cnt;
   }
   if (last_block(st)) {
-    for (int i = threadIdx.x; i < nvec; i += BS) {
-      double d = gather_partials(partials, i);
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x >> 5; i < nvec; i += BS / 32) {
+      double d = warp_gather_partials(partials, i);
+      if (lane != 0) continue;
       if (i <= j) {
         double h = st->sigma[i] * d;
         if (PASS == 0) st->H[j * (MAX_M + 1) + i] = h;
@@ -474,8 +483,9 @@ k_gs_axpy(GmresState* st, double* __restrict__ V, int64_t ldv, int64_t N, double
   double v[1] = {nrm};
   block_sum_store<1>(v, partials + int64_t(blockIdx.x) * PL);
   if (last_block(st)) {
+    double n2 = 0.0;
+    if (threadIdx.x < 32) n2 = warp_gather_partials(partials, 0);
     if (threadIdx.x == 0) {
-      double n2 = gather_partials(partials, 0);
       if (PASS == 0 && (st->eta2 < 0.0 || n2 < st->eta2 * st->wnorm2)) {
         st->reorth = 1;
       } else {
@@ -530,8 +540,10 @@ __global__ void k_loop_ctrl(GmresState* st, cudaGraphConditionalHandle h) {
 // Right-hand sides and FGMRES initialisation (x = 0, V_0 = b, sigma_0 = 1/||b||)
 // ---------------------------------------------------------------------------
 __device__ void gmres_init_last(GmresState* st, double* partials, int m, int max_it, double rtol, double eta2) {
+  double b2 = 0.0;
+  if (threadIdx.x < 32) b2 = warp_gather_partials(partials, 0);
   if (threadIdx.x == 0) {
-    double beta = sqrt(gather_partials(partials, 0));
+    double beta = sqrt(b2);
     st->bnorm = beta;
     st->bnorm_true = beta;
     st->rtol = rtol;
@@ -865,8 +877,10 @@ k_left_start(GmresState* st, const TZ* __restrict__ Zt, double* __restrict__ V, 
   double v1[1] = {nrm};
   block_sum_store<1>(v1, partials + int64_t(blockIdx.x) * PL);
   if (last_block(st)) {
+    double n0sq = 0.0;
+    if (threadIdx.x < 32) n0sq = warp_gather_partials(partials, 0);
     if (threadIdx.x == 0) {
-      double n0 = sqrt(gather_partials(partials, 0));
+      double n0 = sqrt(n0sq);
       double beta = n0 * st->bnorm;          // ||P^{-1} b||
       st->bnorm_true = st->bnorm;
       st->bnorm = beta;
@@ -955,8 +969,10 @@ k_left_residual(GmresState* st, const double* __restrict__ V, int64_t ldv, doubl
   double v1[1] = {nrm};
   block_sum_store<1>(v1, partials + int64_t(blockIdx.x) * PL);
   if (last_block(st)) {
+    double b2 = 0.0;
+    if (threadIdx.x < 32) b2 = warp_gather_partials(partials, 0);
     if (threadIdx.x == 0) {
-      double beta = sqrt(gather_partials(partials, 0));
+      double beta = sqrt(b2);
       st->wnorm2 = beta;   // handed to k_left_restart
       st->counter = 0;
     }
