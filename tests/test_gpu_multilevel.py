@@ -137,6 +137,59 @@ def test_mesh_independent_counts_in_the_paper_time_step_scaling(B):
     assert abs(got - oits) <= max(1, int(np.ceil(0.1 * oits))), (got, oits)
 
 
+def test_coarse_w_cycle_through_step_adjoint_and_batch(B):
+    """The W-cycle below the finest level on the library's whole paths: heat
+    97^2 with the coarsest level at most 16 rows (four or more levels),
+    h_t = 4 (stiffness-dominated blocks), Radau IIA s = 3, P_LD, FP32 AMG.  A
+    step within 1e-8 of the oracle's exact stage solve and its iteration count
+    within 10 % of the oracle's FGMRES with the same cycle; an adjoint step
+    within 1e-8 of the oracle's exact one; a batch of two instances (61^2 and
+    97^2) equal to the per-instance runs."""
+    from paper_2010_11377_gb300 import problems
+    s, h, nsteps, every = 3, 4.0, 4, 2
+    A, b, c = B.irk_butcher_table("radau_iia", s)
+    OA, Ob, _ = obt.radau_iia(s)
+    opts = dict(kind="LD", cycle="Wc", coarse_max=16)
+    ctxs, meshes = [], []
+    for N in (61, 97):
+        p = problems.heat(N)
+        ctxs.append(B.irk_setup(p["rowptr"], p["col"], p["valM"], p["valF"], (A, b, c), h,
+                                options=B.irk_default_options(**opts), g=p["g"]))
+        meshes.append(p["mesh"])
+    ctx, mesh = ctxs[1], meshes[1]
+    rows, _ = B.irk_amg_info(ctx, 0)
+    assert len(rows) >= 4, rows
+    prob = ofem.heat_problem(mesh)
+    u0 = synth.heat_u0(mesh)
+    u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(u)
+    st = B.irk_step(ctx, u, out)
+    assert st["resid"] <= 1e-10
+    ref = oirk.IRKSolver(prob, OA, Ob, h, kind=None).step(u0, direct=True).u
+    assert np.linalg.norm(out.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+    oits = oirk.IRKSolver(prob, OA, Ob, h, kind="LD", subsolve="amg",
+                          amg_opts=dict(cycle="Wc", coarse_max=16)).step(u0).iterations
+    assert abs(st["iterations"] - oits) <= max(1, int(np.ceil(0.1 * oits))), (st["iterations"], oits)
+    lam1 = synth.random_smooth_u0(mesh, seed=3)
+    lam = torch.empty_like(u)
+    B.irk_adjoint_step(ctx, torch.tensor(lam1, dtype=torch.float64, device="cuda"), None, None, lam)
+    ref_lam, _ = oirk.IRKSolver(prob, OA, Ob, h, kind=None).adjoint_step(lam1, direct=True)
+    assert np.linalg.norm(lam.cpu().numpy() - ref_lam) <= 1e-8 * np.linalg.norm(ref_lam)
+    u0s = [torch.tensor(synth.heat_u0(m), dtype=torch.float64, device="cuda") for m in meshes]
+    uNs = [torch.empty_like(x) for x in u0s]
+    cks = [torch.empty(nsteps // every, m.n, dtype=torch.float64, device="cuda") for m in meshes]
+    batch = B.irk_batch_create(ctxs, nsteps, every, u0s, uNs, cks)
+    stats, _ = B.irk_batch_run(batch)
+    assert all(x["steps"] == nsteps and x["resid"] <= 1e-10 for x in stats)
+    for q, cq in enumerate(ctxs):
+        uN = torch.empty_like(uNs[q])
+        B.irk_run(cq, u0s[q], nsteps, uN)
+        assert torch.allclose(uN, uNs[q], rtol=0, atol=1e-14 * float(uN.abs().max()))
+    batch.close()
+    for cq in ctxs:
+        cq.close()
+
+
 def test_operator_without_pairs_child_process(B):
     """The FP32-AMG step with the operator in FP64 products (IRK_KRON_FF=0, a
     child process) is within 1e-8 of the exact solve, like the pair operator."""
