@@ -169,6 +169,7 @@ def _setup_one_unknown(L, o, null_rowptr=False):
 
 @pytest.mark.parametrize("field,value", [("reorth_eta", 1.0), ("reorth_eta", -0.1), ("reorth", 2),
                                          ("restart", 0), ("coarse_max", 4096), ("cheb_degree", 0), ("p_smooth", 0), ("p_smooth", 4), ("strength", 2),
+                                         ("cycle", 2), ("cycle", -1),
                                          ("side", 2), ("kind", 6), ("kind", -1), ("smoother", 2),
                                          ("cheb_lo", 0.0), ("cheb_lo", 1.0), ("cheb_lo", float("nan")),
                                          ("theta", -0.1), ("theta", float("nan")), ("max_levels", 0),
@@ -344,4 +345,7 @@ def test_default_options_as_documented(L):
     assert (o.cheb_degree, o.cheb_lo, o.nu_pre, o.nu_post) == (4, 0.1, 1, 1)
     assert (o.theta, o.coarse_max, o.max_levels) == (0.08, 2048, 12)
     assert (o.restart, o.rtol, o.max_it) == (30, 1e-10, 1000)
-    assert (o.reorth, o.reorth_eta, o.side, o.p_smooth, o.strength) == (0, 0.1, 0, 2, 0)
+    assert (o.reorth, o.reorth_eta, o.side, o.p_smooth, o.strength, o.cycle) == (0, 0.1, 0, 2, 0, 0)
+    assert o.cycle == enum["IRK_CYCLE_V"]
+    from paper_2010_11377_gb300.binding import irk_default_options
+    assert irk_default_options(cycle="Wc").cycle == enum["IRK_CYCLE_W_COARSE"]
