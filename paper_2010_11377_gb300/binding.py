@@ -71,6 +71,11 @@ def irk_atilde(kind: str, A):
 
 
 def irk_default_options(**overrides) -> IrkOptions:
+    """irk_options filled by the library's defaults, then any field overridden by keyword
+    (the names of include/irk.h).  Symbolic values: kind "J", "GSL", "GSL_OPT", "DU", "LD",
+    "CUSTOM"; amg_prec "f64", "f32", "bf16"; side "right", "left"; smoother "l1jacobi",
+    "chebyshev"; cycle "V" (one V-cycle per subsolve) or "Wc" (the W-cycle below the finest
+    level).  Values are checked by irk_setup, not here."""
     o = IrkOptions()
     lib().irk_default_options(C.byref(o))
     for k, v in overrides.items():
